@@ -1,0 +1,111 @@
+"""Physics pins of the FP64 oracle: the nonlinear coefficient beta = 1 + B/2A
+that Eq. 2 implies (Fubini's pre-shock harmonics of a plane wave), the
+emitted amplitude of the additive mass source, and a PML sanity check (the
+paper gives no PML profile, so the PML itself stays unpinned)."""
+
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+from scipy.special import jv
+
+import oracle
+
+C0, RHO0, DZ, DT, F0 = 1500.0, 1000.0, 5e-5, 1e-8, 1e6   # 30 points per wavelength, 100 steps per period
+
+
+def _plane_wave_run(amp, bona, nonlinear, z_src, probes, nz, steps, ramp_cycles=3):
+    """4 x 4 x nz grid, PML only on z, additive mass source filling the plane
+    z = z_src with a ramped sinusoid; returns the last two periods of p at the
+    probe planes."""
+    flags = oracle.NONLINEAR if nonlinear else 0
+    g = oracle.Grid(4, 4, nz, DZ, DZ, DZ, DT, C0, pml_size=(0, 0, 10), pml_alpha=(0, 0, 2.0),
+                    flags=flags)
+    sim = oracle.Simulation(g)
+    sim.set_medium(C0, RHO0, bona, 0.0)
+    t = (np.arange(steps) + 0.5) * DT
+    ramp = np.clip(t * F0 / ramp_cycles, 0, 1)
+    ramp = 0.5 - 0.5 * np.cos(np.pi * ramp)
+    sig = amp * ramp * np.sin(2 * np.pi * F0 * t)
+    yy, xx = np.meshgrid(np.arange(4), np.arange(4), indexing="ij")
+    idx = (xx + 4 * (yy + 4 * z_src)).ravel()
+    sim.add_source(idx, sig)
+    rec = []
+    for n in range(steps):
+        sim.step(1)
+        if n >= steps - 200:
+            rec.append([sim.p[z, 1, 1] for z in probes])
+    return np.array(rec)           # (200, n_probes)
+
+
+def _harmonics(series, nmax):
+    n = len(series)
+    tt = np.arange(n)
+    return np.array([2 * abs(np.sum(series * np.exp(-2j * np.pi * h * tt / 100))) / n
+                     for h in range(1, nmax + 1)])
+
+
+def test_source_emits_its_signal_amplitude():
+    """Reading R10: a planar additive mass source radiates a plane wave whose
+    amplitude equals the signal amplitude (linear, 30 points per wavelength)."""
+    z_src = 14
+    probes = [z_src + 30, z_src + 60]
+    rec = _plane_wave_run(1.0, 0.0, False, z_src, probes, 128, 700)
+    for j in range(len(probes)):
+        a1 = _harmonics(rec[:, j], 1)[0]
+        assert abs(a1 - 1.0) <= 0.01, a1
+
+
+def test_fubini_harmonics():
+    """Eq. 2: the model's plane-wave nonlinearity coefficient is beta = 1 + B/2A.
+    Before the shock, harmonic n of a sinusoidal plane wave is
+    B_n / p_s = 2 J_n(n sigma) / (n sigma), sigma = z / x_sh,
+    x_sh = rho0 c0^3 / (beta omega p_s) (Fubini's solution).
+
+    The additive source's own near field moves the effective origin of the
+    distortion (by about a third of a wavelength); one origin offset sigma0 is
+    fitted to B_2 at a near probe, then all five harmonics at two far probes
+    must follow Fubini.  A wrong beta changes how fast the harmonics grow
+    between the probes (beta = B/2A or 1 + B/A fail by more than 10 %)."""
+    bona = 10.0
+    beta = 1.0 + bona / 2.0
+    amp = 5e6
+    z_src = 14
+    x_sh_nom = RHO0 * C0 ** 3 / (beta * 2 * np.pi * F0 * amp)
+    zs = [z_src + 30] + [z_src + int(round(s * x_sh_nom / DZ)) for s in (0.15, 0.35, 0.6)]
+    nz = zs[-1] + 60
+    steps = int((zs[-1] - z_src) / 0.3) + 600
+    rec = _plane_wave_run(amp, bona, True, z_src, zs, nz, steps)
+    p_s = _harmonics(rec[:, 0], 1)[0]
+    x_sh = RHO0 * C0 ** 3 / (beta * 2 * np.pi * F0 * p_s)
+
+    def fub(n, s):
+        return 2 * jv(n, n * s) / (n * s)
+
+    b2 = _harmonics(rec[:, 1], 2)[1] / p_s
+    s_eff = brentq(lambda s: fub(2, s) - b2, 1e-4, 1.0)
+    sigma0 = (zs[1] - z_src) * DZ / x_sh - s_eff
+    assert 0 <= sigma0 < 0.05, sigma0          # a fraction of a wavelength
+    for j in (2, 3):
+        sigma = (zs[j] - z_src) * DZ / x_sh - sigma0
+        got = _harmonics(rec[:, j], 5) / p_s
+        for n in range(5):
+            tol = 0.03 if n < 3 else 0.06
+            assert abs(got[n] / fub(n + 1, sigma) - 1) <= tol, (sigma, n + 1, got[n])
+
+
+def test_pml_reflection_below_minus_35_db():
+    """Sanity check only (the paper gives no PML profile): a plane pulse that
+    runs into the z PML returns less than -35 dB of its amplitude."""
+    nz = 160
+    g = oracle.Grid(4, 4, nz, DZ, DZ, DZ, DT, C0, pml_size=(0, 0, 10), pml_alpha=(0, 0, 2.0))
+    sim = oracle.Simulation(g)
+    sim.set_medium(C0, RHO0)
+    z = np.arange(nz)
+    p0 = np.exp(-((z - nz / 2) ** 2) / (2 * 4.0 ** 2))
+    sim.set_initial_pressure(np.broadcast_to(p0.reshape(nz, 1, 1), g.shape))
+    # each half-pulse (amplitude 0.5) reaches the PML after ~70 cells; give it time to return
+    sim.step(int(2 * (nz / 2) / 0.3) + 40)
+    interior = np.abs(sim.p[15:nz - 15, 1, 1]).max()
+    assert 20 * math.log10(interior / 0.5) < -35.0, interior
