@@ -1,0 +1,204 @@
+/*
+ * kwgb.h -- C ABI of the GB300 k-space pseudospectral time step.
+ *
+ * The library advances the coupled first-order acoustic equations of
+ * Jaros, Rendell & Treeby, "Full-wave nonlinear ultrasound simulation on
+ * distributed clusters with applications in HIFU" (Sec. 2, Eqs. 1-8) on one
+ * GPU: 3D real-to-complex / complex-to-real FFTs, the kappa k-space
+ * correction and staggered-grid shift operators (Eqs. 4a, 4c), the split-field
+ * PML velocity and density updates (Eqs. 4b, 4d), the power-law absorption
+ * term (Eq. 8) and the nonlinear equation of state (Eq. 6).
+ *
+ * Conventions
+ *  - Grid arrays are float32, C order [nz][ny][nx] (x fastest); the linear
+ *    index of (x, y, z) is x + nx * (y + ny * z).
+ *  - u_xi is stored at the staggered point x_i + dxi/2 (Sec. 2.2, Fig. 1).
+ *  - Every input array is COPIED by the library; the caller keeps ownership.
+ *    Input pointers are host pointers unless the call says otherwise.
+ *  - Functions return KWGB_OK (0) or a negative KWGB_ERR_* code; the message
+ *    of the last failure on a simulation is returned by kwgb_last_error().
+ *    Nothing traps or aborts on the device; device-side problems (non-finite
+ *    pressure) raise a flag that the next synchronising call reports.
+ *  - kwgb_step() is asynchronous on the caller's CUDA stream; kwgb_read(),
+ *    kwgb_read_field() and kwgb_status() synchronise with it.
+ *  - Supported grids: nx, ny, nz powers of two in [8, 1024] (the FFT passes
+ *    are radix-2^k shared-memory kernels); anything else is KWGB_ERR_UNSUPPORTED.
+ *  - Calls on one simulation are not thread safe; separate simulations are
+ *    independent.
+ */
+#ifndef KWGB_H
+#define KWGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define KWGB_OK                0
+#define KWGB_ERR_ARG          -1  /* invalid argument (null, size, range)      */
+#define KWGB_ERR_OOM          -2  /* device allocation failed                  */
+#define KWGB_ERR_CUDA         -3  /* a CUDA runtime call failed                */
+#define KWGB_ERR_NONFINITE    -4  /* pressure became NaN/Inf during stepping   */
+#define KWGB_ERR_TIMEOUT      -5  /* a bounded device wait ran out             */
+#define KWGB_ERR_STATE        -6  /* call not allowed in the current state     */
+#define KWGB_ERR_UNSUPPORTED  -7  /* valid request the library does not serve  */
+
+/* ---- grid flags (kwgb_grid_desc.flags) ---------------------------------- */
+#define KWGB_NONLINEAR   1u  /* Eq. 4d denominator and (B/2A) rho^2/rho0 of Eq. 6 */
+#define KWGB_ABSORBING   2u  /* power-law absorption/dispersion L_d of Eq. 8     */
+
+/* ---- sensor outputs (kwgb_add_sensor record / kwgb_read which) ---------- */
+#define KWGB_P_MAX  1u   /* max_n p^n, n = 1..Nt                               */
+#define KWGB_P_RMS  2u   /* sqrt(mean_n (p^n)^2)                               */
+#define KWGB_I_AVG  4u   /* time-averaged intensity, 3 components per point    */
+
+/* ---- source modes ------------------------------------------------------- */
+#define KWGB_ADDITIVE_MASS 0  /* mass source M of Eq. 4d, see kwgb_add_source  */
+
+/* ---- kwgb_set_medium scalar_mask bits ----------------------------------- */
+#define KWGB_SCALAR_C0      1u
+#define KWGB_SCALAR_RHO0    2u
+#define KWGB_SCALAR_BONA    4u
+#define KWGB_SCALAR_ALPHA0  8u
+#define KWGB_INPUT_DEVICE   0x80000000u /* non-scalar arrays are device pointers */
+
+/* ---- fields for kwgb_read_field ----------------------------------------- */
+#define KWGB_FIELD_P     0   /* p^n                  */
+#define KWGB_FIELD_UX    1   /* u_x^{n-1/2}          */
+#define KWGB_FIELD_UY    2
+#define KWGB_FIELD_UZ    3
+#define KWGB_FIELD_RHOX  4   /* rho_x^n (split field) */
+#define KWGB_FIELD_RHOY  5
+#define KWGB_FIELD_RHOZ  6
+
+/* ---- spectral operators for kwgb_apply_operator ------------------------- */
+#define KWGB_OP_GRAD_FWD 0   /* Eq. 4a: IFT{ i k_xi kappa e^{+i k_xi dxi/2} FT{f} }, 3 outputs */
+#define KWGB_OP_GRAD_BWD 1   /* Eq. 4c: IFT{ i k_xi kappa e^{-i k_xi dxi/2} FT{f} }, 3 outputs */
+#define KWGB_OP_ABS_TAU  2   /* Eq. 8:  IFT{ k^{y-2} FT{f} }, 1 output (0 at k = 0)           */
+#define KWGB_OP_ABS_ETA  3   /* Eq. 8:  IFT{ k^{y-1} FT{f} }, 1 output (0 at k = 0)           */
+
+typedef struct kwgb_sim kwgb_sim;  /* opaque; owned by the library */
+
+/* Grid and run parameters (Sec. 2.2; Eq. 5 wavenumbers).
+ *   nx, ny, nz    grid points (powers of two, 8..1024)
+ *   dx, dy, dz    spacing [m];  dt  time step [s]
+ *   c_ref         reference sound speed of kappa = sinc(c_ref k dt/2) [m/s]
+ *   pml_size      PML thickness in cells per axis (0 = none), inside the grid
+ *   pml_alpha     PML strength per axis [Np per grid point]; the absorption is
+ *                 alpha * (c_ref/dxi) * (depth/size)^4, depth measured in cells
+ *                 from the inner edge of the layer
+ *   flags         KWGB_NONLINEAR | KWGB_ABSORBING
+ *   alpha_power   power-law exponent y (Eq. 3), 0 < y < 3, y != 1; one value
+ *                 for the whole grid                                          */
+typedef struct {
+    int64_t nx, ny, nz;
+    double dx, dy, dz, dt, c_ref;
+    int32_t pml_size[3];
+    double pml_alpha[3];
+    uint32_t flags;
+    double alpha_power;
+} kwgb_grid_desc;
+
+/* Validate desc and create an empty simulation.  No device memory is taken
+ * until kwgb_set_medium().  *out receives the handle (NULL on failure).
+ * Errors: ARG (null, non-positive spacing or dt, PML too thick, y outside
+ * (0,3) or y == 1 when absorbing), UNSUPPORTED (sizes). */
+int kwgb_create(const kwgb_grid_desc* desc, kwgb_sim** out);
+
+/* Route the simulation's device allocations through alloc/free (for example
+ * a framework's caching allocator).  alloc(bytes, ctx) returns a device
+ * pointer aligned to 256 bytes or NULL; free(ptr, ctx) releases it.  Must be
+ * called before kwgb_set_medium().  Errors: ARG, STATE. */
+int kwgb_set_allocator(kwgb_sim* sim, void* (*alloc)(size_t bytes, void* ctx),
+                       void (*free_fn)(void* ptr, void* ctx), void* ctx);
+
+/* Medium (Eq. 1/3): sound speed c0 [m/s], ambient density rho0 [kg/m^3],
+ * nonlinearity B/A, and the power-law prefactor alpha0 in
+ * Np (rad/s)^-y m^-1.  Each pointer refers to nx*ny*nz floats, or to one
+ * float when its KWGB_SCALAR_* bit is set in scalar_mask; b_on_a and alpha0
+ * may be NULL (= 0).  With KWGB_INPUT_DEVICE set, the non-scalar arrays are
+ * device pointers (scalars are always host).  Allocates all device state
+ * and zeroes p, u, rho.  Errors: ARG, OOM, CUDA, STATE (already set). */
+int kwgb_set_medium(kwgb_sim* sim, const float* c0, const float* rho0,
+                    const float* b_on_a, const float* alpha0, uint32_t scalar_mask);
+
+/* Initial pressure p0 (host, nx*ny*nz floats).  Sets p^0 = p0,
+ * rho_xi^0 = p0/(3 c0^2) and u_xi^{-1/2} = +dt/(2 rho0_sg) d/dxi p0 (Eq. 4a
+ * operator), so that the velocity is zero at t = 0.  Before the first step
+ * only.  Errors: ARG, STATE, CUDA. */
+int kwgb_set_initial_pressure(kwgb_sim* sim, const float* p0);
+
+/* Additive mass source (the M term of Eq. 4d) at n_idx linear indices idx
+ * (host int64, each in [0, nx*ny*nz)).  signal (host) holds n_signals rows
+ * of n_t samples: n_signals == 1 drives every point with the same signal,
+ * n_signals == n_idx gives point i its own row.  Sample n drives time step n
+ * (t = (n + 1/2) dt); after n_t steps the source is silent.  At each point
+ * every split density gets rho_xi += dt * 2 s / (3 c0 dx), so a planar source
+ * radiates a plane wave of amplitude s.  Points may repeat and sources may
+ * overlap (contributions add).  Before the first step only.
+ * *source_id receives the source number.  Errors: ARG, STATE, OOM, CUDA. */
+int kwgb_add_source(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
+                    const float* signal, int64_t n_signals, int64_t n_t,
+                    int mode, int32_t* source_id);
+
+/* Sensor at n_idx linear indices idx (host int64), or at every grid point
+ * when idx is NULL (then n_idx is ignored).  record is a set of KWGB_P_MAX,
+ * KWGB_P_RMS, KWGB_I_AVG.  Samples are p^1 .. p^Nt.  Before the first step
+ * only.  *sensor_id receives the sensor number.  Errors: ARG, STATE, OOM. */
+int kwgb_add_sensor(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
+                    uint32_t record, int32_t* sensor_id);
+
+/* Advance n_steps time steps, (u^{n-1/2}, rho^n, p^n) -> (u^{n+1/2},
+ * rho^{n+1}, p^{n+1}) per step, asynchronously on cuda_stream (a
+ * cudaStream_t; NULL = the legacy default stream).  n_steps == 0 is a no-op.
+ * Errors: ARG (n_steps < 0), STATE (no medium), CUDA. */
+int kwgb_step(kwgb_sim* sim, int64_t n_steps, void* cuda_stream);
+
+/* Copy one sensor output to host_out as float64.  which is ONE of
+ * KWGB_P_MAX (n_idx values), KWGB_P_RMS (n_idx values) or KWGB_I_AVG
+ * (3*n_idx values: all x components, then y, then z).  n is the capacity of
+ * host_out in doubles.  Synchronises.  The intensity's last term needs
+ * u^{Nt+1/2}; it is computed here by one extra velocity update that changes
+ * no state.  With no step taken p_max = -inf, p_rms = 0, I = 0.
+ * Errors: ARG (bad id/which, n too small, output not recorded), CUDA,
+ * NONFINITE (pressure went non-finite; the values are still copied). */
+int kwgb_read(kwgb_sim* sim, int32_t sensor_id, uint32_t which,
+              double* host_out, int64_t n);
+
+/* Copy a state field (KWGB_FIELD_*) at the current step to host_out
+ * (nx*ny*nz floats).  Synchronises.  Errors: ARG, STATE, CUDA, NONFINITE. */
+int kwgb_read_field(kwgb_sim* sim, int field, float* host_out, int64_t n);
+
+/* Apply one of the step's spectral operators (KWGB_OP_*) to the device field
+ * in (nx*ny*nz floats) and write the result(s) to the device arrays out0..2
+ * (out1/out2 only for the gradient operators), on cuda_stream, using the
+ * simulation's grid and scratch spectra.  The state is not touched.  Needs
+ * kwgb_set_medium() first.  Errors: ARG, STATE, CUDA. */
+int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float* out0,
+                        float* out1, float* out2, void* cuda_stream);
+
+/* Number of steps taken so far. */
+int64_t kwgb_steps_done(const kwgb_sim* sim);
+
+/* Synchronise and report device-side status: KWGB_OK, KWGB_ERR_NONFINITE
+ * or KWGB_ERR_CUDA. */
+int kwgb_status(kwgb_sim* sim);
+
+/* Device bytes held by the simulation. */
+int64_t kwgb_device_bytes(const kwgb_sim* sim);
+
+/* Message describing the last failure on sim ("" if none); with sim == NULL,
+ * the last failure of kwgb_create.  Valid until the next call on sim. */
+const char* kwgb_last_error(const kwgb_sim* sim);
+
+/* Release the simulation and all its device memory.  NULL is a no-op. */
+void kwgb_destroy(kwgb_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KWGB_H */

@@ -1,0 +1,754 @@
+// C-ABI implementation: validation, device buffers, the 1-D tables (built on
+// the host in float64), the sparse source/sensor structures, and the launch
+// sequence of one time step.
+//
+// Device memory of a simulation (F = nx*ny*nz floats, S = nz*ny*nhp complex):
+//   u_x, u_y, u_z, rho_x, rho_y, rho_z        6 F   state
+//   c0, rho0, B/A, alpha0                     <= 4 F (scalars take no memory)
+//   P (x-transformed p^n), T1, T2, T3         4 S   spectra; T1/T2 hold the
+//                                                   step's temporaries, T3 is
+//                                                   scratch for reads and
+//                                                   kwgb_apply_operator
+//   sensors, sources, 1-D tables              small
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/kwgb.h"
+#include "kwgb_internal.h"
+
+using namespace kwgb;
+
+static constexpr double kPi = 3.14159265358979323846;
+
+namespace {
+
+struct HostSource {
+    std::vector<int64_t> idx;
+    std::vector<float> sig;
+    int64_t nsig, nt;
+};
+
+struct HostSensor {
+    bool full;
+    std::vector<int64_t> idx;   // masked points
+    uint32_t record;
+    int64_t n;                  // number of points
+    int64_t slot0;              // first slot (masked)
+    int full_k;                 // index into the full-grid arrays
+    int64_t i0;                 // first entry in the intensity list (-1: none)
+};
+
+thread_local std::string g_create_error;
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int64_t v) { int l = 0; while ((int64_t(1) << l) < v) ++l; return l; }
+
+}  // namespace
+
+struct kwgb_sim {
+    kwgb_grid_desc d;
+    GridC g;
+    Medium md;
+    std::string err;
+    void* (*alloc)(size_t, void*) = nullptr;
+    void (*freef)(void*, void*) = nullptr;
+    void* actx = nullptr;
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    bool medium_set = false;
+    bool frozen = false;
+    int64_t steps = 0;
+    int64_t N = 0;              // grid points
+    size_t spec_elems = 0;      // complex elements per spectrum
+
+    float* u[3] = {nullptr, nullptr, nullptr};
+    float* rho[3] = {nullptr, nullptr, nullptr};
+    float2* P = nullptr;
+    float2* T1 = nullptr;
+    float2* T2 = nullptr;
+    float2* T3 = nullptr;
+    int64_t* d_step = nullptr;
+    int* d_flag = nullptr;
+
+    std::vector<HostSource> hsrc;
+    std::vector<HostSensor> hsens;
+    SourceC src{};
+    SensorC sens{};
+    int64_t n_slots = 0;
+    int64_t n_i = 0;            // intensity points
+    int64_t* i_idx = nullptr;
+    int32_t* i_slot = nullptr;
+    double* I = nullptr;
+    double* I_tail = nullptr;
+    float* ubuf = nullptr;
+    cudaStream_t last_stream = nullptr;
+};
+
+// ------------------------------------------------------------------ helpers
+static int fail(kwgb_sim* s, int code, const std::string& msg) {
+    if (s) s->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(sim, KWGB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void* dalloc(kwgb_sim* sim, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (sim->alloc) {
+        p = sim->alloc(bytes, sim->actx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        sim->allocs.push_back(p);
+        sim->bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+template <class T>
+static T* dalloc_t(kwgb_sim* sim, size_t n) { return static_cast<T*>(dalloc(sim, n * sizeof(T))); }
+
+#define DALLOC(ptr, T, n)                                                              \
+    do {                                                                               \
+        ptr = dalloc_t<T>(sim, (size_t)(n));                                           \
+        if (!ptr) return fail(sim, KWGB_ERR_OOM, "device allocation failed: " #ptr);   \
+    } while (0)
+
+template <class T>
+static int upload(kwgb_sim* sim, T** dst, const std::vector<T>& src) {
+    DALLOC(*dst, T, src.size());
+    if (!src.empty()) CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return KWGB_OK;
+}
+
+// Eq. 5 wavenumber of DFT bin j of an axis with n points and spacing d
+static double wavenumber(int64_t j, int64_t n, double d) {
+    const int64_t m = (n % 2 == 0) ? (j < n / 2 ? j : j - n) : (j <= (n - 1) / 2 ? j : j - n);
+    return (double)m * 2.0 * kPi / (d * (double)n);
+}
+
+// PML factor exp(-a dt / 2), a = alpha * (c_ref / d) * (depth / size)^4
+static double pml_factor(double s, int64_t n, int size, double alpha, double c_ref, double d, double dt) {
+    if (size <= 0) return 1.0;
+    const double depth = std::max(0.0, std::max((double)size - s, s - (double)(n - 1 - size)));
+    const double a = alpha * (c_ref / d) * std::pow(depth / size, 4.0);
+    return std::exp(-a * dt / 2.0);
+}
+
+// ------------------------------------------------------------------ create
+extern "C" int kwgb_create(const kwgb_grid_desc* desc, kwgb_sim** out) {
+    g_create_error.clear();
+    auto bad = [&](int code, const char* m) { g_create_error = m; if (out) *out = nullptr; return code; };
+    if (!desc || !out) return bad(KWGB_ERR_ARG, "null argument");
+    const int64_t n[3] = {desc->nx, desc->ny, desc->nz};
+    const double dd[3] = {desc->dx, desc->dy, desc->dz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] <= 0) return bad(KWGB_ERR_ARG, "grid sizes must be positive");
+        if (!is_pow2(n[a]) || n[a] < 8 || n[a] > 1024)
+            return bad(KWGB_ERR_UNSUPPORTED, "grid sizes must be powers of two in [8, 1024]");
+        if (!(dd[a] > 0) || !std::isfinite(dd[a])) return bad(KWGB_ERR_ARG, "spacing must be positive");
+        if (desc->pml_size[a] < 0 || 2 * (int64_t)desc->pml_size[a] >= n[a])
+            return bad(KWGB_ERR_ARG, "pml_size must be >= 0 and leave an interior");
+        if (!(desc->pml_alpha[a] >= 0) || !std::isfinite(desc->pml_alpha[a]))
+            return bad(KWGB_ERR_ARG, "pml_alpha must be >= 0");
+    }
+    if (!(desc->dt > 0) || !std::isfinite(desc->dt)) return bad(KWGB_ERR_ARG, "dt must be positive");
+    if (!(desc->c_ref > 0) || !std::isfinite(desc->c_ref)) return bad(KWGB_ERR_ARG, "c_ref must be positive");
+    if (desc->flags & ~(KWGB_NONLINEAR | KWGB_ABSORBING)) return bad(KWGB_ERR_ARG, "unknown flag bits");
+    if (desc->flags & KWGB_ABSORBING) {
+        const double y = desc->alpha_power;
+        if (!(y > 0 && y < 3) || y == 1.0) return bad(KWGB_ERR_ARG, "alpha_power must be in (0,3), != 1");
+    }
+    kwgb_sim* sim = new (std::nothrow) kwgb_sim();
+    if (!sim) return bad(KWGB_ERR_OOM, "host allocation failed");
+    sim->d = *desc;
+    GridC& g = sim->g;
+    std::memset(&g, 0, sizeof(g));
+    g.nx = (int)n[0]; g.ny = (int)n[1]; g.nz = (int)n[2];
+    g.nh = g.nx / 2 + 1;
+    g.nhp = (g.nh + 15) / 16 * 16;
+    g.lognx = ilog2(n[0]); g.logny = ilog2(n[1]); g.lognz = ilog2(n[2]);
+    g.dt = (float)desc->dt;
+    sim->N = n[0] * n[1] * n[2];
+    g.scale = (float)(1.0 / (double)sim->N);
+    g.hk = (float)(desc->c_ref * desc->dt / 2.0);
+    const double y = desc->alpha_power;
+    double kmax2 = 0;
+    for (int a = 0; a < 3; ++a) kmax2 += (kPi / dd[a]) * (kPi / dd[a]);
+    g.inv_kmax2 = (float)(1.0 / kmax2);
+    g.abs_e[0] = (float)((y - 2.0) / 2.0);
+    g.abs_e[1] = (float)((y - 1.0) / 2.0);
+    g.abs_c[0] = (float)std::pow(std::sqrt(kmax2), y - 2.0);
+    g.abs_c[1] = (float)std::pow(std::sqrt(kmax2), y - 1.0);
+    sim->spec_elems = (size_t)g.nhp * g.ny * g.nz;
+    Medium& md = sim->md;
+    std::memset(&md, 0, sizeof(md));
+    md.y = (float)y;
+    md.tan_pi_y_2 = (float)std::tan(kPi * y / 2.0);
+    md.nonlinear = (desc->flags & KWGB_NONLINEAR) ? 1 : 0;
+    md.absorbing = (desc->flags & KWGB_ABSORBING) ? 1 : 0;
+    *out = sim;
+    return KWGB_OK;
+}
+
+extern "C" int kwgb_set_allocator(kwgb_sim* sim, void* (*alloc)(size_t, void*),
+                                  void (*free_fn)(void*, void*), void* ctx) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (sim->medium_set) return fail(sim, KWGB_ERR_STATE, "allocator must be set before kwgb_set_medium");
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(sim, KWGB_ERR_ARG, "alloc and free go together");
+    sim->alloc = alloc;
+    sim->freef = free_fn;
+    sim->actx = ctx;
+    return KWGB_OK;
+}
+
+// ------------------------------------------------------------------ medium
+static int build_tables(kwgb_sim* sim) {
+    const kwgb_grid_desc& d = sim->d;
+    GridC& g = sim->g;
+    const int64_t n[3] = {d.nx, d.ny, d.nz};
+    const double dd[3] = {d.dx, d.dy, d.dz};
+    std::vector<float2> tw(1024);
+    for (int t = 0; t < 1024; ++t) {
+        const double a = 2.0 * kPi * t / 1024.0;
+        tw[t] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    float2* dtw;
+    if (int e = upload(sim, &dtw, tw)) return e;
+    g.t.tw = dtw;
+    const int64_t klen[3] = {g.nh, d.ny, d.nz};
+    for (int a = 0; a < 3; ++a) {
+        std::vector<float> k(klen[a]);
+        std::vector<float2> df(klen[a]);
+        for (int64_t j = 0; j < klen[a]; ++j) {
+            const double kk = wavenumber(j, n[a], dd[a]);
+            k[j] = (float)kk;
+            // i k exp(+i k d / 2) = (-k sin(k d / 2), k cos(k d / 2))
+            df[j] = make_float2((float)(-kk * std::sin(kk * dd[a] / 2.0)), (float)(kk * std::cos(kk * dd[a] / 2.0)));
+        }
+        float* dk;
+        float2* ddf;
+        if (int e = upload(sim, &dk, k)) return e;
+        if (int e = upload(sim, &ddf, df)) return e;
+        if (a == 0) { g.t.kx = dk; g.t.dfx = ddf; }
+        if (a == 1) { g.t.ky = dk; g.t.dfy = ddf; }
+        if (a == 2) { g.t.kz = dk; g.t.dfz = ddf; }
+        std::vector<float> f(n[a]), fs(n[a]);
+        for (int64_t i = 0; i < n[a]; ++i) {
+            f[i] = (float)pml_factor((double)i, n[a], d.pml_size[a], d.pml_alpha[a], d.c_ref, dd[a], d.dt);
+            fs[i] = (float)pml_factor((double)i + 0.5, n[a], d.pml_size[a], d.pml_alpha[a], d.c_ref, dd[a], d.dt);
+        }
+        float *df1, *df2;
+        if (int e = upload(sim, &df1, f)) return e;
+        if (int e = upload(sim, &df2, fs)) return e;
+        g.t.pml[a] = df1;
+        g.t.pml_sg[a] = df2;
+    }
+    return KWGB_OK;
+}
+
+static int set_field(kwgb_sim* sim, const float* src, bool scalar, bool dev, float* scal_out,
+                     const float** field_out, float dflt) {
+    *field_out = nullptr;
+    if (src == nullptr) { *scal_out = dflt; return KWGB_OK; }
+    if (scalar) {
+        *scal_out = *src;
+        if (!std::isfinite(*scal_out)) return fail(sim, KWGB_ERR_ARG, "non-finite medium scalar");
+        return KWGB_OK;
+    }
+    float* p;
+    DALLOC(p, float, sim->N);
+    CK(cudaMemcpy(p, src, sim->N * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    *field_out = p;
+    *scal_out = 0.f;
+    return KWGB_OK;
+}
+
+extern "C" int kwgb_set_medium(kwgb_sim* sim, const float* c0, const float* rho0,
+                               const float* b_on_a, const float* alpha0, uint32_t scalar_mask) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (sim->medium_set) return fail(sim, KWGB_ERR_STATE, "medium already set");
+    if (!c0 || !rho0) return fail(sim, KWGB_ERR_ARG, "c0 and rho0 are required");
+    const bool dev = (scalar_mask & KWGB_INPUT_DEVICE) != 0;
+    if ((scalar_mask & KWGB_SCALAR_C0) && !(*c0 > 0)) return fail(sim, KWGB_ERR_ARG, "c0 must be positive");
+    if ((scalar_mask & KWGB_SCALAR_RHO0) && !(*rho0 > 0)) return fail(sim, KWGB_ERR_ARG, "rho0 must be positive");
+    int dev_id = 0;
+    CK(cudaGetDevice(&dev_id));
+    Medium& md = sim->md;
+    int e;
+    if ((e = set_field(sim, c0, scalar_mask & KWGB_SCALAR_C0, dev, &md.c0_s, &md.c0, 0.f))) return e;
+    if ((e = set_field(sim, rho0, scalar_mask & KWGB_SCALAR_RHO0, dev, &md.rho0_s, &md.rho0, 0.f))) return e;
+    if ((e = set_field(sim, b_on_a, scalar_mask & KWGB_SCALAR_BONA, dev, &md.bona_s, &md.bona, 0.f))) return e;
+    if ((e = set_field(sim, alpha0, scalar_mask & KWGB_SCALAR_ALPHA0, dev, &md.alpha0_s, &md.alpha0, 0.f))) return e;
+    if ((e = build_tables(sim))) return e;
+    const size_t N = (size_t)sim->N;
+    for (int a = 0; a < 3; ++a) {
+        DALLOC(sim->u[a], float, N);
+        DALLOC(sim->rho[a], float, N);
+        CK(cudaMemset(sim->u[a], 0, N * sizeof(float)));
+        CK(cudaMemset(sim->rho[a], 0, N * sizeof(float)));
+    }
+    DALLOC(sim->P, float2, sim->spec_elems);
+    DALLOC(sim->T1, float2, sim->spec_elems);
+    DALLOC(sim->T2, float2, sim->spec_elems);
+    DALLOC(sim->T3, float2, sim->spec_elems);
+    CK(cudaMemset(sim->P, 0, sim->spec_elems * sizeof(float2)));
+    DALLOC(sim->d_step, int64_t, 1);
+    DALLOC(sim->d_flag, int, 1);
+    CK(cudaMemset(sim->d_step, 0, sizeof(int64_t)));
+    CK(cudaMemset(sim->d_flag, 0, sizeof(int)));
+    CK(cudaDeviceSynchronize());
+    sim->medium_set = true;
+    return KWGB_OK;
+}
+
+// ------------------------------------------------------------------ launch helpers
+#define LK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(sim, KWGB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// spectrum -> gradient spectra (x still transformed): y fwd, z op, y inv
+static int grad_chain(kwgb_sim* sim, float2* in, float2* const out[3], int kind, cudaStream_t s) {
+    const GridC& g = sim->g;
+    float2* i1[1] = {in};
+    LK(launch_y_pass(g, -1, i1, i1, 1, s));
+    float2* zin[3] = {in, nullptr, nullptr};
+    LK(launch_z_op(g, kind, zin, out, s));
+    LK(launch_y_pass(g, +1, out, out, 3, s));
+    return KWGB_OK;
+}
+
+static SensorC sensor_c(kwgb_sim* sim) { return sim->sens; }
+
+static int launch_step(kwgb_sim* sim, cudaStream_t s) {
+    const GridC& g = sim->g;
+    float2* sp[3] = {sim->P, sim->T1, sim->T2};
+    StepC st{sim->d_step, sim->d_flag};
+    // Eq. 4a: y fwd of x-transformed p, z fwd + operator + z inv (3 outputs), y inv
+    {
+        float2* i1[1] = {sim->P};
+        LK(launch_y_pass(g, -1, i1, i1, 1, s));
+        float2* zin[3] = {sim->P, nullptr, nullptr};
+        LK(launch_z_op(g, Z_GRAD_FWD, zin, sp, s));
+        LK(launch_y_pass(g, +1, sp, sp, 3, s));
+    }
+    if (sim->n_i) LK(launch_intensity_gather(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, s));
+    // Eq. 4b (+ x R2C of u), Eq. 4c (y fwd, z fwd + operator + z inv, y inv)
+    XVelArgs va{};
+    for (int a = 0; a < 3; ++a) { va.G[a] = sp[a]; va.u[a] = sim->u[a]; va.U[a] = sp[a]; }
+    LK(launch_x_vel(g, sim->md, XV_STEP, va, s));
+    if (sim->n_i)
+        LK(launch_intensity_accum(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, sim->sens.p_sens,
+                                  sim->i_slot, sim->I, sim->d_step, 1, s));
+    LK(launch_y_pass(g, -1, sp, sp, 3, s));
+    LK(launch_z_op(g, Z_DIV, sp, sp, s));
+    LK(launch_y_pass(g, +1, sp, sp, 3, s));
+    // Eq. 4d + source; lossless: Eq. 6 + sensors + R2C of p here
+    XDensArgs da{};
+    for (int a = 0; a < 3; ++a) { da.D[a] = sp[a]; da.rho[a] = sim->rho[a]; }
+    const SensorC sens = sensor_c(sim);
+    if (sim->md.absorbing) {
+        da.S = sim->P;
+        da.R = sim->T1;
+        da.rho_tot = reinterpret_cast<float*>(sim->T2);
+        LK(launch_x_dens(g, sim->md, sim->src, sens, st, da, s));
+        // Eq. 8: y fwd, z fwd + k^{y-2} / k^{y-1} + z inv, y inv, then Eq. 6
+        float2* ab[3] = {sim->P, sim->T1, nullptr};
+        LK(launch_y_pass(g, -1, ab, ab, 2, s));
+        LK(launch_z_op(g, Z_ABS, ab, ab, s));
+        LK(launch_y_pass(g, +1, ab, ab, 2, s));
+        XEosArgs ea{sim->P, sim->T1, reinterpret_cast<float*>(sim->T2), sim->P};
+        LK(launch_x_eos(g, sim->md, sens, st, ea, s));
+    } else {
+        da.P = sim->P;
+        LK(launch_x_dens(g, sim->md, sim->src, sens, st, da, s));
+    }
+    LK(launch_advance_step(sim->d_step, s));
+    return KWGB_OK;
+}
+
+// ------------------------------------------------------------------ initial pressure
+extern "C" int kwgb_set_initial_pressure(kwgb_sim* sim, const float* p0) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (!p0) return fail(sim, KWGB_ERR_ARG, "p0 is null");
+    if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
+    if (sim->steps > 0) return fail(sim, KWGB_ERR_STATE, "initial pressure after stepping");
+    const GridC& g = sim->g;
+    cudaStream_t s = nullptr;
+    float* real3 = reinterpret_cast<float*>(sim->T3);
+    const int rp = 2 * g.nhp;
+    CK(cudaMemcpy2D(real3, rp * sizeof(float), p0, g.nx * sizeof(float), g.nx * sizeof(float),
+                    (size_t)g.ny * g.nz, cudaMemcpyHostToDevice));
+    LK(launch_init_rho(g, sim->md, real3, rp, sim->rho, s));
+    // u^{-1/2} = +dt / (2 rho0_sg) d/dxi p0
+    LK(launch_x_r2c(g, real3, rp, sim->P, s));
+    float2* out[3] = {sim->T3, sim->T1, sim->T2};
+    if (int e = grad_chain(sim, sim->P, out, Z_GRAD_FWD, s)) return e;
+    XVelArgs va{};
+    for (int a = 0; a < 3; ++a) { va.G[a] = out[a]; va.u[a] = sim->u[a]; }
+    LK(launch_x_vel(g, sim->md, XV_INIT, va, s));
+    // P = x-R2C of p0 again (the chain above consumed it)
+    CK(cudaMemcpy2D(real3, rp * sizeof(float), p0, g.nx * sizeof(float), g.nx * sizeof(float),
+                    (size_t)g.ny * g.nz, cudaMemcpyHostToDevice));
+    LK(launch_x_r2c(g, real3, rp, sim->P, s));
+    CK(cudaDeviceSynchronize());
+    return KWGB_OK;
+}
+
+// ------------------------------------------------------------------ sources and sensors
+extern "C" int kwgb_add_source(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
+                               const float* signal, int64_t n_signals, int64_t n_t,
+                               int mode, int32_t* source_id) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (sim->frozen || sim->steps > 0) return fail(sim, KWGB_ERR_STATE, "sources must be added before stepping");
+    if (mode != KWGB_ADDITIVE_MASS) return fail(sim, KWGB_ERR_UNSUPPORTED, "only additive mass sources");
+    if (n_idx < 0 || n_t < 0) return fail(sim, KWGB_ERR_ARG, "negative size");
+    if (n_idx > 0 && (!idx || (n_t > 0 && !signal))) return fail(sim, KWGB_ERR_ARG, "null idx or signal");
+    if (!(n_signals == 1 || n_signals == n_idx)) return fail(sim, KWGB_ERR_ARG, "n_signals must be 1 or n_idx");
+    HostSource hs;
+    hs.idx.assign(idx, idx + n_idx);
+    for (int64_t v : hs.idx)
+        if (v < 0 || v >= sim->N) return fail(sim, KWGB_ERR_ARG, "source index out of range");
+    hs.nsig = n_signals;
+    hs.nt = n_t;
+    if (n_t > 0 && n_idx > 0) hs.sig.assign(signal, signal + n_signals * n_t);
+    sim->hsrc.push_back(std::move(hs));
+    if (source_id) *source_id = (int32_t)sim->hsrc.size() - 1;
+    return KWGB_OK;
+}
+
+extern "C" int kwgb_add_sensor(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
+                               uint32_t record, int32_t* sensor_id) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (sim->frozen || sim->steps > 0) return fail(sim, KWGB_ERR_STATE, "sensors must be added before stepping");
+    if (record == 0 || (record & ~(KWGB_P_MAX | KWGB_P_RMS | KWGB_I_AVG)))
+        return fail(sim, KWGB_ERR_ARG, "bad record flags");
+    HostSensor hs{};
+    hs.record = record;
+    hs.i0 = -1;
+    if (idx == nullptr) {
+        int nfull = 0;
+        for (auto& o : sim->hsens) nfull += o.full ? 1 : 0;
+        if ((record & KWGB_I_AVG) || nfull >= 4) {
+            // full-grid intensity (or a fifth full-grid sensor): list every point
+            hs.full = false;
+            hs.idx.resize(sim->N);
+            std::iota(hs.idx.begin(), hs.idx.end(), int64_t(0));
+        } else {
+            hs.full = true;
+        }
+        hs.n = sim->N;
+    } else {
+        if (n_idx < 0) return fail(sim, KWGB_ERR_ARG, "negative size");
+        hs.full = false;
+        hs.idx.assign(idx, idx + n_idx);
+        for (int64_t v : hs.idx)
+            if (v < 0 || v >= sim->N) return fail(sim, KWGB_ERR_ARG, "sensor index out of range");
+        hs.n = n_idx;
+    }
+    sim->hsens.push_back(std::move(hs));
+    if (sensor_id) *sensor_id = (int32_t)sim->hsens.size() - 1;
+    return KWGB_OK;
+}
+
+// Build the device source/sensor structures (once, at the first step).
+static int freeze(kwgb_sim* sim) {
+    if (sim->frozen) return KWGB_OK;
+    const int64_t nx = sim->g.nx;
+    const int64_t nrows = (int64_t)sim->g.ny * sim->g.nz;
+    // ---- sources: contributions sorted by grid index, unique points per row
+    struct Contrib { int64_t L; int64_t off; int32_t nt; };
+    std::vector<Contrib> cs;
+    std::vector<float> sig;
+    for (auto& s : sim->hsrc) {
+        const int64_t base = (int64_t)sig.size();
+        sig.insert(sig.end(), s.sig.begin(), s.sig.end());
+        for (size_t i = 0; i < s.idx.size(); ++i)
+            cs.push_back({s.idx[i], base + (s.nsig == 1 ? 0 : (int64_t)i * s.nt), (int32_t)s.nt});
+    }
+    if (!cs.empty()) {
+        std::stable_sort(cs.begin(), cs.end(), [](const Contrib& a, const Contrib& b) { return a.L < b.L; });
+        std::vector<int32_t> row_ptr(nrows + 1, 0), pt_x, pt_c;
+        std::vector<int64_t> c_off;
+        std::vector<int32_t> c_nt;
+        std::vector<float> c_scale;
+        // dt M_xi = dt * 2 s / (3 c0 dx); the kernel divides by c0
+        const float sc = (float)(sim->d.dt * 2.0 / (3.0 * sim->d.dx));
+        for (size_t i = 0; i < cs.size(); ++i) {
+            if (i == 0 || cs[i].L != cs[i - 1].L) {
+                pt_x.push_back((int32_t)(cs[i].L % nx));
+                pt_c.push_back((int32_t)c_off.size());
+                row_ptr[cs[i].L / nx + 1]++;
+            }
+            c_off.push_back(cs[i].off);
+            c_nt.push_back(cs[i].nt);
+            c_scale.push_back(sc);
+        }
+        pt_c.push_back((int32_t)c_off.size());
+        for (int64_t r = 0; r < nrows; ++r) row_ptr[r + 1] += row_ptr[r];
+        int32_t *d_rp, *d_px, *d_pc, *d_cnt;
+        int64_t* d_coff;
+        float *d_cs, *d_sig;
+        if (int e = upload(sim, &d_rp, row_ptr)) return e;
+        if (int e = upload(sim, &d_px, pt_x)) return e;
+        if (int e = upload(sim, &d_pc, pt_c)) return e;
+        if (int e = upload(sim, &d_coff, c_off)) return e;
+        if (int e = upload(sim, &d_cnt, c_nt)) return e;
+        if (int e = upload(sim, &d_cs, c_scale)) return e;
+        if (sig.empty()) sig.push_back(0.f);
+        if (int e = upload(sim, &d_sig, sig)) return e;
+        sim->src = SourceC{d_rp, d_px, d_pc, d_coff, d_cnt, d_cs, d_sig};
+    }
+    // ---- sensors
+    SensorC& sc = sim->sens;
+    sc = SensorC{};
+    struct Entry { int64_t L; int32_t slot; };
+    std::vector<Entry> es;
+    std::vector<int64_t> ii;
+    std::vector<int32_t> islot;
+    int64_t slots = 0;
+    for (auto& h : sim->hsens) {
+        if (h.full) {
+            h.full_k = sc.nfull;
+            DALLOC(sc.full_max[sc.nfull], float, sim->N);
+            DALLOC(sc.full_p2[sc.nfull], double, sim->N);
+            LK(launch_fill_f32(sc.full_max[sc.nfull], sim->N, -INFINITY, nullptr));
+            CK(cudaMemset(sc.full_p2[sc.nfull], 0, sim->N * sizeof(double)));
+            sc.nfull++;
+            continue;
+        }
+        h.slot0 = slots;
+        for (int64_t i = 0; i < h.n; ++i) es.push_back({h.idx[i], (int32_t)(slots + i)});
+        if (h.record & KWGB_I_AVG) {
+            h.i0 = (int64_t)ii.size();
+            for (int64_t i = 0; i < h.n; ++i) { ii.push_back(h.idx[i]); islot.push_back((int32_t)(slots + i)); }
+        }
+        slots += h.n;
+    }
+    sim->n_slots = slots;
+    if (!es.empty()) {
+        std::stable_sort(es.begin(), es.end(), [](const Entry& a, const Entry& b) { return a.L < b.L; });
+        std::vector<int32_t> row_ptr(nrows + 1, 0), ex, eslot;
+        for (auto& e : es) {
+            row_ptr[e.L / nx + 1]++;
+            ex.push_back((int32_t)(e.L % nx));
+            eslot.push_back(e.slot);
+        }
+        for (int64_t r = 0; r < nrows; ++r) row_ptr[r + 1] += row_ptr[r];
+        int32_t *d_rp, *d_ex, *d_es;
+        if (int e = upload(sim, &d_rp, row_ptr)) return e;
+        if (int e = upload(sim, &d_ex, ex)) return e;
+        if (int e = upload(sim, &d_es, eslot)) return e;
+        sc.row_ptr = d_rp;
+        sc.e_x = d_ex;
+        sc.e_slot = d_es;
+        DALLOC(sc.p_max, float, slots);
+        DALLOC(sc.p2, double, slots);
+        DALLOC(sc.p_sens, float, slots);
+        LK(launch_fill_f32(sc.p_max, slots, -INFINITY, nullptr));
+        CK(cudaMemset(sc.p2, 0, slots * sizeof(double)));
+        CK(cudaMemset(sc.p_sens, 0, slots * sizeof(float)));
+    }
+    sim->n_i = (int64_t)ii.size();
+    if (sim->n_i) {
+        if (int e = upload(sim, &sim->i_idx, ii)) return e;
+        if (int e = upload(sim, &sim->i_slot, islot)) return e;
+        DALLOC(sim->I, double, 3 * sim->n_i);
+        DALLOC(sim->I_tail, double, 3 * sim->n_i);
+        DALLOC(sim->ubuf, float, 6 * sim->n_i);
+        CK(cudaMemset(sim->I, 0, 3 * sim->n_i * sizeof(double)));
+    }
+    CK(cudaDeviceSynchronize());
+    sim->frozen = true;
+    return KWGB_OK;
+}
+
+// ------------------------------------------------------------------ stepping
+extern "C" int kwgb_step(kwgb_sim* sim, int64_t n_steps, void* cuda_stream) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (n_steps < 0) return fail(sim, KWGB_ERR_ARG, "n_steps < 0");
+    if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
+    if (n_steps == 0) return KWGB_OK;
+    if (int e = freeze(sim)) return e;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sim->last_stream = s;
+    for (int64_t i = 0; i < n_steps; ++i) {
+        if (int e = launch_step(sim, s)) return e;
+        sim->steps++;
+    }
+    return KWGB_OK;
+}
+
+extern "C" int64_t kwgb_steps_done(const kwgb_sim* sim) { return sim ? sim->steps : 0; }
+
+static int sync_and_flag(kwgb_sim* sim) {
+    CK(cudaStreamSynchronize(sim->last_stream));
+    CK(cudaDeviceSynchronize());
+    int flag = 0;
+    if (sim->d_flag) CK(cudaMemcpy(&flag, sim->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & 1) return fail(sim, KWGB_ERR_NONFINITE, "pressure became non-finite");
+    return KWGB_OK;
+}
+
+extern "C" int kwgb_status(kwgb_sim* sim) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (!sim->medium_set) return KWGB_OK;
+    return sync_and_flag(sim);
+}
+
+// ------------------------------------------------------------------ reading
+extern "C" int kwgb_read(kwgb_sim* sim, int32_t sensor_id, uint32_t which, double* host_out, int64_t n) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (sensor_id < 0 || sensor_id >= (int32_t)sim->hsens.size()) return fail(sim, KWGB_ERR_ARG, "bad sensor id");
+    if (!host_out) return fail(sim, KWGB_ERR_ARG, "null output");
+    HostSensor& h = sim->hsens[sensor_id];
+    if (!(which == KWGB_P_MAX || which == KWGB_P_RMS || which == KWGB_I_AVG))
+        return fail(sim, KWGB_ERR_ARG, "which must be one of P_MAX, P_RMS, I_AVG");
+    if (!(h.record & which)) return fail(sim, KWGB_ERR_ARG, "output not recorded by this sensor");
+    const int64_t need = which == KWGB_I_AVG ? 3 * h.n : h.n;
+    if (n < need) return fail(sim, KWGB_ERR_ARG, "output buffer too small");
+    const int64_t nt = sim->steps;
+    if (nt == 0 || !sim->frozen) {
+        for (int64_t i = 0; i < need; ++i) host_out[i] = which == KWGB_P_MAX ? -INFINITY : 0.0;
+        return KWGB_OK;
+    }
+    int status = sync_and_flag(sim);
+    if (status == KWGB_ERR_CUDA) return status;
+    const SensorC& sc = sim->sens;
+    if (which == KWGB_P_MAX) {
+        std::vector<float> t(h.n);
+        const float* src = h.full ? sc.full_max[h.full_k] : sc.p_max + h.slot0;
+        CK(cudaMemcpy(t.data(), src, h.n * sizeof(float), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < h.n; ++i) host_out[i] = t[i];
+    } else if (which == KWGB_P_RMS) {
+        const double* src = h.full ? sc.full_p2[h.full_k] : sc.p2 + h.slot0;
+        CK(cudaMemcpy(host_out, src, h.n * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < h.n; ++i) host_out[i] = std::sqrt(host_out[i] / (double)nt);
+    } else {
+        // tail term p^{Nt} (ubar^{Nt-1/2} + ubar^{Nt+1/2}) / 2 with u^{Nt+1/2} from one
+        // velocity update that is not stored
+        const GridC& g = sim->g;
+        cudaStream_t s = nullptr;
+        float2* out[3] = {sim->T3, sim->T1, sim->T2};
+        float2* yi[1] = {sim->T3};
+        float2* pin[1] = {sim->P};
+        LK(launch_y_pass(g, -1, pin, yi, 1, s));                  // out of place: P is kept
+        float2* zin[3] = {sim->T3, nullptr, nullptr};
+        LK(launch_z_op(g, Z_GRAD_FWD, zin, out, s));
+        LK(launch_y_pass(g, +1, out, out, 3, s));
+        XVelArgs va{};
+        for (int a = 0; a < 3; ++a) {
+            va.G[a] = out[a];
+            va.u[a] = sim->u[a];
+            va.tail[a] = reinterpret_cast<float*>(out[a]);
+        }
+        LK(launch_x_vel(g, sim->md, XV_TAIL, va, s));
+        CK(cudaMemset(sim->I_tail, 0, 3 * sim->n_i * sizeof(double)));
+        LK(launch_intensity_gather(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, s));
+        float* tails[3] = {reinterpret_cast<float*>(out[0]), reinterpret_cast<float*>(out[1]),
+                           reinterpret_cast<float*>(out[2])};
+        LK(launch_intensity_accum(sim->n_i, sim->i_idx, g, tails, 2 * g.nhp, sim->ubuf, sc.p_sens,
+                                  sim->i_slot, sim->I_tail, sim->d_step, 0, s));
+        CK(cudaDeviceSynchronize());
+        std::vector<double> a(3 * sim->n_i), b(3 * sim->n_i);
+        CK(cudaMemcpy(a.data(), sim->I, a.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(b.data(), sim->I_tail, b.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int xi = 0; xi < 3; ++xi)
+            for (int64_t i = 0; i < h.n; ++i) {
+                const int64_t k = xi * sim->n_i + h.i0 + i;
+                host_out[xi * h.n + i] = (a[k] + b[k]) / (double)nt;
+            }
+    }
+    return status;
+}
+
+extern "C" int kwgb_read_field(kwgb_sim* sim, int field, float* host_out, int64_t n) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "no state yet");
+    if (!host_out || n < sim->N) return fail(sim, KWGB_ERR_ARG, "output buffer too small");
+    if (field < KWGB_FIELD_P || field > KWGB_FIELD_RHOZ) return fail(sim, KWGB_ERR_ARG, "bad field");
+    int status = sync_and_flag(sim);
+    if (status == KWGB_ERR_CUDA) return status;
+    const GridC& g = sim->g;
+    if (field == KWGB_FIELD_P) {
+        float* real3 = reinterpret_cast<float*>(sim->T3);
+        LK(launch_x_c2r(g, sim->P, real3, 2 * g.nhp, nullptr));
+        CK(cudaDeviceSynchronize());
+        // the C2R is unnormalised along x: divide by nx
+        std::vector<float> rows((size_t)g.ny * g.nz * g.nx);
+        CK(cudaMemcpy2D(rows.data(), g.nx * sizeof(float), real3, 2 * g.nhp * sizeof(float),
+                        g.nx * sizeof(float), (size_t)g.ny * g.nz, cudaMemcpyDeviceToHost));
+        const float inv = 1.0f / (float)g.nx;
+        for (size_t i = 0; i < rows.size(); ++i) host_out[i] = rows[i] * inv;
+    } else {
+        const float* src = field <= KWGB_FIELD_UZ ? sim->u[field - 1] : sim->rho[field - 4];
+        CK(cudaMemcpy(host_out, src, sim->N * sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    return status;
+}
+
+extern "C" int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float* out0,
+                                   float* out1, float* out2, void* cuda_stream) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
+    if (!in || !out0) return fail(sim, KWGB_ERR_ARG, "null field");
+    const GridC& g = sim->g;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sim->last_stream = s;
+    if (op == KWGB_OP_GRAD_FWD || op == KWGB_OP_GRAD_BWD) {
+        if (!out1 || !out2) return fail(sim, KWGB_ERR_ARG, "gradient needs three outputs");
+        LK(launch_x_r2c(g, in, g.nx, sim->T3, s));
+        float2* outs[3] = {sim->T3, sim->T1, sim->T2};
+        if (int e = grad_chain(sim, sim->T3, outs, op == KWGB_OP_GRAD_FWD ? Z_GRAD_FWD : Z_GRAD_BWD, s)) return e;
+        float* r[3] = {out0, out1, out2};
+        for (int a = 0; a < 3; ++a) LK(launch_x_c2r(g, outs[a], r[a], g.nx, s));
+        return KWGB_OK;
+    }
+    if (op == KWGB_OP_ABS_TAU || op == KWGB_OP_ABS_ETA) {
+        LK(launch_x_r2c(g, in, g.nx, sim->T3, s));
+        float2* a1[1] = {sim->T3};
+        LK(launch_y_pass(g, -1, a1, a1, 1, s));
+        float2* zin[3] = {nullptr, nullptr, nullptr};
+        zin[op == KWGB_OP_ABS_TAU ? 0 : 1] = sim->T3;
+        LK(launch_z_op(g, Z_ABS, zin, zin, s));
+        LK(launch_y_pass(g, +1, a1, a1, 1, s));
+        LK(launch_x_c2r(g, sim->T3, out0, g.nx, s));
+        return KWGB_OK;
+    }
+    return fail(sim, KWGB_ERR_ARG, "unknown operator");
+}
+
+extern "C" int64_t kwgb_device_bytes(const kwgb_sim* sim) { return sim ? sim->bytes : 0; }
+
+extern "C" const char* kwgb_last_error(const kwgb_sim* sim) {
+    return sim ? sim->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" void kwgb_destroy(kwgb_sim* sim) {
+    if (!sim) return;
+    if (sim->medium_set) cudaDeviceSynchronize();
+    for (void* p : sim->allocs) {
+        if (sim->freef) sim->freef(p, sim->actx);
+        else cudaFree(p);
+    }
+    delete sim;
+}

@@ -1,0 +1,537 @@
+// Contiguous-axis (x) passes: complex-to-real and real-to-complex transforms
+// of whole rows, fused with the pointwise work of the time step so that the
+// real-space fields only ever exist in registers:
+//
+//   x_vel   C2R of the three gradient spectra (Eq. 4a) -> velocity update with
+//           PML (Eq. 4b) -> R2C of the new u_xi (first stage of Eq. 4c)
+//   x_dens  C2R of the three divergence spectra (Eq. 4c) -> split density
+//           update with PML and nonlinear denominator (Eq. 4d) -> additive
+//           mass source -> rho = sum rho_xi and rho0 sum d -> R2C of both
+//           (first stage of Eq. 8); for a lossless medium the EOS (Eq. 6),
+//           the sensors and the R2C of p are done here as well
+//   x_eos   C2R of the two absorption spectra (Eq. 8) -> EOS (Eq. 6) ->
+//           sensors -> R2C of p^{n+1} (first stage of the next Eq. 4a)
+//
+// A row of nx reals is treated as M = nx/2 complex values z[n] = x[2n] +
+// i x[2n+1]; an M-point FFT plus one post-processing step pairing bins k and
+// M-k gives the nx/2+1 bins of the real transform (and the reverse for C2R).
+// TL = M/E threads own a row; thread j holds z[j + TL*m], i.e. the float2 at
+// x = 2(j + TL*m), so every global access of a row is coalesced.
+#include "fft_core.cuh"
+#include "kwgb_internal.h"
+
+namespace kwgb {
+
+constexpr int XTHREADS = 256;
+
+template <int LOGM>
+struct XShape {
+    static constexpr int M = 1 << LOGM;
+    static constexpr int E = M >= 512 ? 16 : (M >= 8 ? 8 : M);
+    static constexpr int TL = M / E;
+    static constexpr int RPB = XTHREADS / TL;        // rows per CTA
+    static constexpr int PITCH = M + M / 16 + 2;     // complex slots per row (padded, + Nyquist)
+    static constexpr int SMEM = RPB * PITCH * (int)sizeof(float2);
+};
+
+struct RowSmem {
+    float2* base;
+    __device__ __forceinline__ float2& at(int e) { return base[e + (e >> 4)]; }
+    __device__ __forceinline__ float& f(int x) { return reinterpret_cast<float*>(base)[x]; }
+    __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+
+// Unnormalised C2R of one row: spec[0..M] (Hermitian half spectrum) ->
+// z[m] = (x[2n], x[2n+1]) with n = j + TL*m and
+// x[i] = sum_{k<nx} X[k] exp(+2 pi i k i / nx).
+template <int LOGM>
+__device__ __forceinline__ void row_c2r(const float2* __restrict__ spec, RowSmem& S, int j,
+                                        bool valid, const float2* __restrict__ tw,
+                                        float2 (&z)[XShape<LOGM>::E]) {
+    using Sh = XShape<LOGM>;
+    constexpr int M = Sh::M, E = Sh::E, TL = Sh::TL;
+    __syncthreads();                                  // smem row free
+    if (valid) {
+        for (int k = j; k <= M; k += TL) S.at(k) = __ldcs(spec + k);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int k = j + TL * m;
+        const float2 xk = S.at(k), xm = cconj(S.at(M - k));
+        const float2 a = cadd(xk, xm);
+        const float2 b = cmul(csub(xk, xm), twiddle1024<+1>(tw, k * (512 / M)));   // exp(+2 pi i k / nx)
+        z[m] = make_float2(a.x - b.y, a.y + b.x);                                // a + i b
+    }
+    line_fft<LOGM, E, +1>(z, j, S, tw);
+}
+
+// Unnormalised R2C of one row: z[m] = (x[2n], x[2n+1]) -> spec[0..M].
+template <int LOGM>
+__device__ __forceinline__ void row_r2c(float2 (&z)[XShape<LOGM>::E], RowSmem& S, int j,
+                                        bool valid, const float2* __restrict__ tw,
+                                        float2* __restrict__ spec) {
+    using Sh = XShape<LOGM>;
+    constexpr int M = Sh::M, E = Sh::E, TL = Sh::TL;
+    line_fft<LOGM, E, -1>(z, j, S, tw);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) S.at(j + TL * m) = z[m];
+    __syncthreads();
+    if (valid) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int k = j + TL * m;
+            const float2 zk = z[m], zm = cconj(S.at((M - k) & (M - 1)));
+            const float2 s = cadd(zk, zm), d = csub(zk, zm);
+            const float2 xe = make_float2(0.5f * s.x, 0.5f * s.y);
+            const float2 xo = make_float2(0.5f * d.y, -0.5f * d.x);              // d / (2i)
+            const float2 x = cadd(xe, cmul(xo, twiddle1024<-1>(tw, k * (512 / M))));
+            __stcs(spec + k, x);
+            if (k == 0) __stcs(spec + M, csub(xe, xo));
+        }
+    }
+}
+
+__device__ __forceinline__ float2 ld2(const float* p) { return __ldcs(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ float2 ldg2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ void st2(float* p, float2 v) { __stcs(reinterpret_cast<float2*>(p), v); }
+
+__device__ __forceinline__ float2 med2(const float* f, float s, size_t i) {
+    return f ? ldg2(f + i) : make_float2(s, s);
+}
+
+// Sensors, non-finite watch and the R2C of p (shared by x_eos and the fused
+// lossless x_dens).  p[m] holds p at x = 2n, 2n+1.
+template <int LOGM>
+__device__ __forceinline__ void finish_pressure(float2 (&p)[XShape<LOGM>::E], const GridC& g,
+                                                const SensorC& sens, const StepC& st,
+                                                RowSmem& S, int j, bool valid, int row,
+                                                float2* __restrict__ P) {
+    using Sh = XShape<LOGM>;
+    constexpr int E = Sh::E, TL = Sh::TL;
+    const size_t rbase = (size_t)row * g.nx;
+    if (valid) {
+        bool bad = false;
+#pragma unroll
+        for (int m = 0; m < E; ++m) bad |= !(isfinite(p[m].x) && isfinite(p[m].y));
+        if (bad) atomicOr(st.flag, 1);
+        for (int k = 0; k < sens.nfull; ++k) {
+            float* pm = sens.full_max[k] + rbase;
+            double* p2 = sens.full_p2[k] + rbase;
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int x = 2 * (j + TL * m);
+                float2 o = *reinterpret_cast<float2*>(pm + x);
+                o.x = fmaxf(o.x, p[m].x);
+                o.y = fmaxf(o.y, p[m].y);
+                *reinterpret_cast<float2*>(pm + x) = o;
+                double2 q = *reinterpret_cast<double2*>(p2 + x);
+                q.x += (double)p[m].x * (double)p[m].x;
+                q.y += (double)p[m].y * (double)p[m].y;
+                *reinterpret_cast<double2*>(p2 + x) = q;
+            }
+        }
+    }
+    if (sens.row_ptr) {                               // uniform over the launch
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int x = 2 * (j + TL * m);
+            S.f(x) = p[m].x;
+            S.f(x + 1) = p[m].y;
+        }
+        __syncthreads();
+        if (valid) {
+            const int e0 = __ldg(sens.row_ptr + row), e1 = __ldg(sens.row_ptr + row + 1);
+            for (int e = e0 + j; e < e1; e += TL) {
+                const int slot = __ldg(sens.e_slot + e);
+                const float v = S.f(__ldg(sens.e_x + e));
+                sens.p_max[slot] = fmaxf(sens.p_max[slot], v);
+                sens.p2[slot] += (double)v * (double)v;
+                sens.p_sens[slot] = v;
+            }
+        }
+    }
+    row_r2c<LOGM>(p, S, j, valid, g.t.tw, P + (size_t)row * g.nhp);
+}
+
+// ---------------------------------------------------------------- x_vel
+struct XVelK {
+    GridC g;
+    Medium md;
+    XVelArgs a;
+};
+
+template <int LOGM, int MODE>
+__global__ void __launch_bounds__(XTHREADS) x_vel_kernel(const XVelK K) {
+    using Sh = XShape<LOGM>;
+    constexpr int E = Sh::E, TL = Sh::TL;
+    extern __shared__ float2 smem[];
+    const GridC& g = K.g;
+    const int r = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int nrows = g.ny * g.nz;
+    const int row = blockIdx.x * Sh::RPB + r;
+    const bool valid = row < nrows;
+    const int rr = valid ? row : 0;
+    const int y = rr % g.ny, z = rr / g.ny;
+    RowSmem S{smem + r * Sh::PITCH};
+    const size_t rb = (size_t)rr * g.nx;
+    const float* rho0 = K.md.rho0;
+    const float rho0s = K.md.rho0_s;
+
+#pragma unroll 1
+    for (int xi = 0; xi < 3; ++xi) {
+        float2 v[E];
+        row_c2r<LOGM>(K.a.G[xi] + (size_t)rr * g.nhp, S, j, valid, g.t.tw, v);
+        // staggered-grid density (mean of the two neighbours along xi) and PML factor
+        size_t nb;                                    // row base of the +1 neighbour along y / z
+        if (xi == 1) nb = (size_t)(((y + 1) & (g.ny - 1)) + g.ny * z) * g.nx;
+        else nb = (size_t)(y + g.ny * ((z + 1) & (g.nz - 1))) * g.nx;
+        const float fyz = xi == 1 ? __ldg(g.t.pml_sg[1] + y) : __ldg(g.t.pml_sg[2] + z);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int x = 2 * (j + TL * m);
+            float2 rs;
+            if (rho0) {
+                const float2 r0 = ldg2(rho0 + rb + x);
+                if (xi == 0) {
+                    const float r2 = __ldg(rho0 + rb + ((x + 2) & (g.nx - 1)));
+                    rs = make_float2(0.5f * (r0.x + r0.y), 0.5f * (r0.y + r2));
+                } else {
+                    const float2 r1 = ldg2(rho0 + nb + x);
+                    rs = make_float2(0.5f * (r0.x + r1.x), 0.5f * (r0.y + r1.y));
+                }
+            } else {
+                rs = make_float2(rho0s, rho0s);
+            }
+            float2 f;
+            if (xi == 0) f = ldg2(g.t.pml_sg[0] + x);
+            else f = make_float2(fyz, fyz);
+            const float2 gr = v[m];
+            float2 un;
+            if (MODE == XV_INIT) {
+                // u^{-1/2} = +dt / (2 rho0_sg) d/dxi p0
+                un = make_float2(0.5f * g.dt * gr.x / rs.x, 0.5f * g.dt * gr.y / rs.y);
+            } else {
+                const float2 uo = valid ? ld2(K.a.u[xi] + rb + x) : make_float2(0.f, 0.f);
+                // Eq. 4b with the PML: u <- f (f u - dt grad p / rho0_sg)
+                un = make_float2(f.x * (f.x * uo.x - g.dt * gr.x / rs.x),
+                                 f.y * (f.y * uo.y - g.dt * gr.y / rs.y));
+            }
+            if (valid) {
+                if (MODE == XV_TAIL) st2(K.a.tail[xi] + (size_t)rr * 2 * g.nhp + x, un);
+                else st2(K.a.u[xi] + rb + x, un);
+            }
+            v[m] = un;
+        }
+        if (MODE == XV_STEP) row_r2c<LOGM>(v, S, j, valid, g.t.tw, K.a.U[xi] + (size_t)rr * g.nhp);
+    }
+}
+
+// ---------------------------------------------------------------- x_dens
+struct XDensK {
+    GridC g;
+    Medium md;
+    SourceC src;
+    SensorC sens;
+    StepC st;
+    XDensArgs a;
+};
+
+template <int LOGM, bool FUSED_EOS>
+__global__ void __launch_bounds__(XTHREADS) x_dens_kernel(const XDensK K) {
+    using Sh = XShape<LOGM>;
+    constexpr int E = Sh::E, TL = Sh::TL;
+    extern __shared__ float2 smem[];
+    const GridC& g = K.g;
+    const Medium& md = K.md;
+    const int r = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int nrows = g.ny * g.nz;
+    const int row = blockIdx.x * Sh::RPB + r;
+    const bool valid = row < nrows;
+    const int rr = valid ? row : 0;
+    const int y = rr % g.ny, z = rr / g.ny;
+    RowSmem S{smem + r * Sh::PITCH};
+    const size_t rb = (size_t)rr * g.nx;
+
+    // additive mass source of this row (dt M_xi, identical for every xi)
+    float2 sv[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) sv[m] = make_float2(0.f, 0.f);
+    if (K.src.row_ptr) {                               // uniform over the launch
+        const int p0 = valid ? __ldg(K.src.row_ptr + rr) : 0;
+        const int p1 = valid ? __ldg(K.src.row_ptr + rr + 1) : 0;
+        const int64_t n = *K.st.step;
+        __syncthreads();
+        if (p1 > p0) {
+            for (int x = j; x < g.nx; x += TL) S.f(x) = 0.f;
+        }
+        __syncthreads();
+        for (int p = p0 + j; p < p1; p += TL) {
+            const int c0 = __ldg(K.src.pt_c + p), c1 = __ldg(K.src.pt_c + p + 1);
+            float acc = 0.f;
+            for (int c = c0; c < c1; ++c) {
+                if (n < __ldg(K.src.c_nt + c))
+                    acc += __ldg(K.src.signal + __ldg(K.src.c_off + c) + n) * __ldg(K.src.c_scale + c);
+            }
+            const int x = __ldg(K.src.pt_x + p);
+            const float c = md.c0 ? __ldg(md.c0 + rb + x) : md.c0_s;
+            S.f(x) = acc / c;                          // dt * 2 s / (3 c0 dx)
+        }
+        __syncthreads();
+        if (p1 > p0) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int x = 2 * (j + TL * m);
+                sv[m] = make_float2(S.f(x), S.f(x + 1));
+            }
+        }
+    }
+
+    float2 r0[E], s[E], rt[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        r0[m] = med2(md.rho0, md.rho0_s, rb + 2 * (j + TL * m));
+        s[m] = make_float2(0.f, 0.f);
+        rt[m] = make_float2(0.f, 0.f);
+    }
+    const float fy = __ldg(g.t.pml[1] + y), fz = __ldg(g.t.pml[2] + z);
+#pragma unroll 1
+    for (int xi = 0; xi < 3; ++xi) {
+        float2 d[E];
+        row_c2r<LOGM>(K.a.D[xi] + (size_t)rr * g.nhp, S, j, valid, g.t.tw, d);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int x = 2 * (j + TL * m);
+            const float2 ro = valid ? ld2(K.a.rho[xi] + rb + x) : make_float2(0.f, 0.f);
+            const float2 f = xi == 0 ? ldg2(g.t.pml[0] + x) : (xi == 1 ? make_float2(fy, fy) : make_float2(fz, fz));
+            // Eq. 4d with the PML: rho_xi <- f (f rho_xi - dt rho0 d) / (1 + 2 dt d)
+            float nx_ = f.x * (f.x * ro.x - g.dt * r0[m].x * d[m].x);
+            float ny_ = f.y * (f.y * ro.y - g.dt * r0[m].y * d[m].y);
+            if (md.nonlinear) {
+                nx_ = nx_ / (1.0f + 2.0f * g.dt * d[m].x);
+                ny_ = ny_ / (1.0f + 2.0f * g.dt * d[m].y);
+            }
+            const float2 rn = make_float2(nx_ + sv[m].x, ny_ + sv[m].y);
+            if (valid) st2(K.a.rho[xi] + rb + x, rn);
+            rt[m] = cadd(rt[m], rn);
+            s[m] = make_float2(fmaf(r0[m].x, d[m].x, s[m].x), fmaf(r0[m].y, d[m].y, s[m].y));
+        }
+    }
+    if (FUSED_EOS) {
+        // Eq. 6 without absorption: p = c0^2 (rho + B/2A rho^2 / rho0)
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const size_t i = rb + 2 * (j + TL * m);
+            const float2 c = med2(md.c0, md.c0_s, i);
+            float2 rho = rt[m];
+            float2 q = rho;
+            if (md.nonlinear) {
+                const float2 ba = med2(md.bona, md.bona_s, i);
+                q.x += 0.5f * ba.x * rho.x * rho.x / r0[m].x;
+                q.y += 0.5f * ba.y * rho.y * rho.y / r0[m].y;
+            }
+            s[m] = make_float2(c.x * c.x * q.x, c.y * c.y * q.y);
+        }
+        finish_pressure<LOGM>(s, g, K.sens, K.st, S, j, valid, rr, K.a.P);
+    } else {
+        if (valid) {
+#pragma unroll
+            for (int m = 0; m < E; ++m)
+                st2(K.a.rho_tot + (size_t)rr * 2 * g.nhp + 2 * (j + TL * m), rt[m]);
+        }
+        row_r2c<LOGM>(s, S, j, valid, g.t.tw, K.a.S + (size_t)rr * g.nhp);
+        row_r2c<LOGM>(rt, S, j, valid, g.t.tw, K.a.R + (size_t)rr * g.nhp);
+    }
+}
+
+// ---------------------------------------------------------------- x_eos
+struct XEosK {
+    GridC g;
+    Medium md;
+    SensorC sens;
+    StepC st;
+    XEosArgs a;
+};
+
+template <int LOGM>
+__global__ void __launch_bounds__(XTHREADS) x_eos_kernel(const XEosK K) {
+    using Sh = XShape<LOGM>;
+    constexpr int E = Sh::E, TL = Sh::TL;
+    extern __shared__ float2 smem[];
+    const GridC& g = K.g;
+    const Medium& md = K.md;
+    const int r = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int nrows = g.ny * g.nz;
+    const int row = blockIdx.x * Sh::RPB + r;
+    const bool valid = row < nrows;
+    const int rr = valid ? row : 0;
+    RowSmem S{smem + r * Sh::PITCH};
+    const size_t rb = (size_t)rr * g.nx;
+    float2 a1[E], a2[E];
+    row_c2r<LOGM>(K.a.A1 + (size_t)rr * g.nhp, S, j, valid, g.t.tw, a1);
+    row_c2r<LOGM>(K.a.A2 + (size_t)rr * g.nhp, S, j, valid, g.t.tw, a2);
+    float2 p[E];
+    const float ym1 = md.y - 1.0f;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int x = 2 * (j + TL * m);
+        const size_t i = rb + x;
+        const float2 rho = valid ? ld2(K.a.rho_tot + (size_t)rr * 2 * g.nhp + x) : make_float2(0.f, 0.f);
+        const float2 c = med2(md.c0, md.c0_s, i);
+        const float2 al = med2(md.alpha0, md.alpha0_s, i);
+        float pv[2];
+        const float cc[2] = {c.x, c.y}, aa[2] = {al.x, al.y}, rr2[2] = {rho.x, rho.y};
+        const float t1[2] = {a1[m].x, a1[m].y}, t2[2] = {a2[m].x, a2[m].y};
+        float2 r0 = make_float2(1.f, 1.f), ba = make_float2(0.f, 0.f);
+        if (md.nonlinear) {
+            r0 = med2(md.rho0, md.rho0_s, i);
+            ba = med2(md.bona, md.bona_s, i);
+        }
+        const float r0a[2] = {r0.x, r0.y}, baa[2] = {ba.x, ba.y};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            // Eq. 3: tau = -2 alpha0 c0^{y-1}, eta = 2 alpha0 c0^y tan(pi y / 2)
+            const float cy1 = exp2f(ym1 * log2f(cc[h]));
+            const float tau = -2.0f * aa[h] * cy1;
+            const float eta = 2.0f * aa[h] * cy1 * cc[h] * md.tan_pi_y_2;
+            // Eq. 8: L_d = -tau IFT{k^{y-2} FT{rho0 sum d}} + eta IFT{k^{y-1} FT{rho}}
+            const float ld = -tau * t1[h] + eta * t2[h];
+            float q = rr2[h];
+            if (md.nonlinear) q += 0.5f * baa[h] * rr2[h] * rr2[h] / r0a[h];
+            pv[h] = cc[h] * cc[h] * (q - ld);                               // Eq. 6
+        }
+        p[m] = make_float2(pv[0], pv[1]);
+    }
+    finish_pressure<LOGM>(p, g, K.sens, K.st, S, j, valid, rr, K.a.P);
+}
+
+// ---------------------------------------------------------------- plain x
+struct XPlainK {
+    GridC g;
+    const float* rin;
+    int rpitch;
+    float2* cout;
+    const float2* cin;
+    float* rout;
+};
+
+template <int LOGM>
+__global__ void __launch_bounds__(XTHREADS) x_r2c_kernel(const XPlainK K) {
+    using Sh = XShape<LOGM>;
+    constexpr int E = Sh::E, TL = Sh::TL;
+    extern __shared__ float2 smem[];
+    const int r = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int row = blockIdx.x * Sh::RPB + r;
+    const bool valid = row < K.g.ny * K.g.nz;
+    const int rr = valid ? row : 0;
+    RowSmem S{smem + r * Sh::PITCH};
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+        v[m] = valid ? ld2(K.rin + (size_t)rr * K.rpitch + 2 * (j + TL * m)) : make_float2(0.f, 0.f);
+    row_r2c<LOGM>(v, S, j, valid, K.g.t.tw, K.cout + (size_t)rr * K.g.nhp);
+}
+
+template <int LOGM>
+__global__ void __launch_bounds__(XTHREADS) x_c2r_kernel(const XPlainK K) {
+    using Sh = XShape<LOGM>;
+    constexpr int E = Sh::E, TL = Sh::TL;
+    extern __shared__ float2 smem[];
+    const int r = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int row = blockIdx.x * Sh::RPB + r;
+    const bool valid = row < K.g.ny * K.g.nz;
+    const int rr = valid ? row : 0;
+    RowSmem S{smem + r * Sh::PITCH};
+    float2 v[E];
+    row_c2r<LOGM>(K.cin + (size_t)rr * K.g.nhp, S, j, valid, K.g.t.tw, v);
+    if (valid) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) st2(K.rout + (size_t)rr * K.rpitch + 2 * (j + TL * m), v[m]);
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <class Kern, class Args>
+static cudaError_t launch_rows(Kern k, int rpb, int smem_bytes, const GridC& g, const Args& args,
+                               cudaStream_t s) {
+    if (smem_bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    const int nrows = g.ny * g.nz;
+    k<<<(nrows + rpb - 1) / rpb, XTHREADS, smem_bytes, s>>>(args);
+    return cudaGetLastError();
+}
+
+#define KWGB_LOGM_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9)
+
+cudaError_t launch_x_vel(const GridC& g, const Medium& m, int mode, const XVelArgs& a,
+                         cudaStream_t s) {
+    XVelK K{g, m, a};
+    switch (g.lognx - 1) {
+#define CASE(L)                                                                                   \
+    case L:                                                                                       \
+        if (mode == XV_STEP) return launch_rows(x_vel_kernel<L, XV_STEP>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s); \
+        if (mode == XV_TAIL) return launch_rows(x_vel_kernel<L, XV_TAIL>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s); \
+        return launch_rows(x_vel_kernel<L, XV_INIT>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s);
+        KWGB_LOGM_CASES(CASE)
+#undef CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src,
+                          const SensorC& sens, const StepC& st, const XDensArgs& a,
+                          cudaStream_t s) {
+    XDensK K{g, m, src, sens, st, a};
+    const bool fused = !m.absorbing;
+    switch (g.lognx - 1) {
+#define CASE(L)                                                                                   \
+    case L:                                                                                       \
+        if (fused) return launch_rows(x_dens_kernel<L, true>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s); \
+        return launch_rows(x_dens_kernel<L, false>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s);
+        KWGB_LOGM_CASES(CASE)
+#undef CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_x_eos(const GridC& g, const Medium& m, const SensorC& sens,
+                         const StepC& st, const XEosArgs& a, cudaStream_t s) {
+    XEosK K{g, m, sens, st, a};
+    switch (g.lognx - 1) {
+#define CASE(L) \
+    case L: return launch_rows(x_eos_kernel<L>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s);
+        KWGB_LOGM_CASES(CASE)
+#undef CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_x_r2c(const GridC& g, const float* in, int in_pitch, float2* out,
+                         cudaStream_t s) {
+    XPlainK K{g, in, in_pitch, out, nullptr, nullptr};
+    switch (g.lognx - 1) {
+#define CASE(L) \
+    case L: return launch_rows(x_r2c_kernel<L>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s);
+        KWGB_LOGM_CASES(CASE)
+#undef CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_x_c2r(const GridC& g, const float2* in, float* out, int out_pitch,
+                         cudaStream_t s) {
+    XPlainK K{g, nullptr, out_pitch, nullptr, in, out};
+    switch (g.lognx - 1) {
+#define CASE(L) \
+    case L: return launch_rows(x_c2r_kernel<L>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s);
+        KWGB_LOGM_CASES(CASE)
+#undef CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace kwgb

@@ -1,0 +1,141 @@
+// Internal declarations shared by the kernel translation units and the C-ABI
+// implementation: parameter blocks passed by value to the kernels and the
+// host-side launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kwgb {
+
+// 1-D tables in device memory (generated on the host in float64, stored as float).
+struct Tables {
+    const float2* tw;         // exp(-2 pi i t / 1024), t < 1024 (FFT twiddles)
+    const float* kx;          // Eq. 5 wavenumbers: kx for the half spectrum (nh values)
+    const float* ky;          //   ky (ny), kz (nz), FFT storage order
+    const float* kz;
+    const float2* dfx;        // i k exp(+i k d / 2) per axis (Eq. 4a shift operator, no kappa)
+    const float2* dfy;
+    const float2* dfz;
+    const float* pml[3];      // PML factor exp(-a dt / 2) on the regular grid, per axis
+    const float* pml_sg[3];   // ... on the staggered grid i + 1/2
+};
+
+struct GridC {
+    int nx, ny, nz;           // grid
+    int nh;                   // nx / 2 + 1 (half-spectrum length along x)
+    int nhp;                  // row pitch of spectra, complex elements (multiple of 16)
+    int lognx, logny, lognz;
+    float dt;
+    float scale;              // 1 / (nx ny nz): inverse-FFT normalisation
+    float hk;                 // c_ref dt / 2, argument factor of kappa
+    float inv_kmax2;          // 1 / max k^2
+    float abs_e[2];           // (y-2)/2, (y-1)/2: powers of k^2 / kmax^2 in Eq. 8
+    float abs_c[2];           // kmax^(y-2), kmax^(y-1)
+    Tables t;
+};
+
+struct Medium {
+    const float* c0;          // NULL -> scalar value below
+    const float* rho0;
+    const float* bona;
+    const float* alpha0;
+    float c0_s, rho0_s, bona_s, alpha0_s;
+    float y;                  // power-law exponent
+    float tan_pi_y_2;         // tan(pi y / 2)
+    int nonlinear, absorbing;
+};
+
+// Sources: unique points per row (CSR over rows), each with a range of
+// contributions (signal row, per-point scale dt * 2 / (3 c0 dx)).
+struct SourceC {
+    const int32_t* row_ptr;   // nrows + 1, NULL when there are no sources
+    const int32_t* pt_x;      // x of each unique point
+    const int32_t* pt_c;      // npts + 1 contribution ranges
+    const int64_t* c_off;     // start of the contribution's signal samples
+    const int32_t* c_nt;      // number of samples
+    const float* c_scale;     // dt * 2 / (3 c0 dx)
+    const float* signal;      // all signal samples
+};
+
+// Masked sensor points (CSR over rows) and full-grid sensors.
+struct SensorC {
+    const int32_t* row_ptr;   // nrows + 1, NULL when no masked sensor points
+    const int32_t* e_x;       // x of each entry
+    const int32_t* e_slot;    // slot of each entry
+    float* p_max;             // per slot
+    double* p2;               // per slot, sum of p^2
+    float* p_sens;            // per slot, last p (intensity)
+    int nfull;                // full-grid sensors (<= 4)
+    float* full_max[4];
+    double* full_p2[4];
+};
+
+struct StepC {
+    const int64_t* step;      // device step counter n (the step maps n -> n+1)
+    int* flag;                // device status bits (1 = non-finite pressure)
+};
+
+// ---- launchers (return the launch error) --------------------------------
+// y pass on ncomp spectra: in[c] -> out[c] (in place allowed); dir -1 forward, +1 inverse
+cudaError_t launch_y_pass(const GridC& g, int dir, float2* const* in, float2* const* out,
+                          int ncomp, cudaStream_t s);
+
+enum ZOpKind { Z_GRAD_FWD = 0, Z_GRAD_BWD = 1, Z_DIV = 2, Z_ABS = 3 };
+// z forward FFT -> operator -> z inverse FFT:
+//   Z_GRAD_*: in[0] -> out[xi] (NULL skips a component)
+//   Z_DIV:    in[xi] -> out[xi]  (Eq. 4c operator)
+//   Z_ABS:    in[0] -> out[0] with k^{y-2}, in[1] -> out[1] with k^{y-1} (NULL skips)
+cudaError_t launch_z_op(const GridC& g, int kind, float2* const* in, float2* const* out,
+                        cudaStream_t s);
+
+enum XVelMode { XV_STEP = 0, XV_TAIL = 1, XV_INIT = 2 };
+struct XVelArgs {
+    const float2* G[3];       // gradient spectra (Eq. 4a, after y/z inverse)
+    float* u[3];              // velocity (pitch nx)
+    float2* U[3];             // XV_STEP: x-R2C of the new velocity (may alias G)
+    float* tail[3];           // XV_TAIL: u^{Nt+1/2} written as real rows of pitch 2*nhp
+};
+cudaError_t launch_x_vel(const GridC& g, const Medium& m, int mode, const XVelArgs& a,
+                         cudaStream_t s);
+
+struct XDensArgs {
+    const float2* D[3];       // divergence spectra (Eq. 4c)
+    float* rho[3];            // split density (pitch nx)
+    float2* S;                // x-R2C of rho0 sum d  (absorbing only)
+    float2* R;                // x-R2C of rho         (absorbing only)
+    float* rho_tot;           // rho as real rows of pitch 2*nhp (absorbing only)
+    float2* P;                // non-absorbing: x-R2C of p (EOS fused here)
+};
+cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src,
+                          const SensorC& sens, const StepC& st, const XDensArgs& a,
+                          cudaStream_t s);
+
+struct XEosArgs {
+    const float2* A1;         // IFT_yz{k^{y-2} ...} of S (x still spectral)
+    const float2* A2;         // ... k^{y-1} of R
+    const float* rho_tot;     // pitch 2*nhp
+    float2* P;                // x-R2C of p^{n+1}
+};
+cudaError_t launch_x_eos(const GridC& g, const Medium& m, const SensorC& sens,
+                         const StepC& st, const XEosArgs& a, cudaStream_t s);
+
+// plain x transforms: real rows (pitch in floats) <-> half spectra (pitch nhp)
+cudaError_t launch_x_r2c(const GridC& g, const float* in, int in_pitch, float2* out,
+                         cudaStream_t s);
+cudaError_t launch_x_c2r(const GridC& g, const float2* in, float* out, int out_pitch,
+                         cudaStream_t s);
+
+// small kernels
+cudaError_t launch_init_rho(const GridC& g, const Medium& m, const float* p0, int p0_pitch,
+                            float* rho[3], cudaStream_t s);
+cudaError_t launch_advance_step(int64_t* step, cudaStream_t s);
+cudaError_t launch_intensity_gather(int64_t n, const int64_t* idx, const GridC& g,
+                                    float* const* u, int pitch, float* ubuf, cudaStream_t s);
+cudaError_t launch_intensity_accum(int64_t n, const int64_t* idx, const GridC& g,
+                                   float* const* u, int pitch, const float* ubuf,
+                                   const float* p_sens, const int32_t* slot, double* I,
+                                   const int64_t* step, int skip_first, cudaStream_t s);
+cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t s);
+
+}  // namespace kwgb

@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI (no GPU): the library builds for sm_103a,
+loads, exports every function include/kwgb.h declares, and validates grid
+descriptors without touching the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1408_4675_gb300 import build, kwgb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return kwgb.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "kwgb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kwgb_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("kwgb_create", "kwgb_set_medium", "kwgb_add_source", "kwgb_add_sensor", "kwgb_step",
+              "kwgb_read", "kwgb_set_allocator", "kwgb_last_error", "kwgb_destroy"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def _desc(**kw):
+    d = kwgb.GridDesc()
+    d.nx, d.ny, d.nz = kw.get("n", (64, 32, 16))
+    d.dx = d.dy = d.dz = 1e-4
+    d.dt, d.c_ref = 2e-8, 1500.0
+    for i in range(3):
+        d.pml_size[i] = kw.get("pml", 4)
+        d.pml_alpha[i] = 2.0
+    d.flags = kw.get("flags", 3)
+    d.alpha_power = kw.get("y", 1.5)
+    return d
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(), 0),
+    (dict(n=(12, 16, 16)), -7),          # not a power of two
+    (dict(n=(2048, 8, 8)), -7),          # too large
+    (dict(n=(4, 8, 8)), -7),             # too small
+    (dict(n=(0, 8, 8)), -1),
+    (dict(pml=8, n=(16, 16, 16)), -1),   # PML leaves no interior
+    (dict(y=1.0), -1),
+    (dict(y=3.5), -1),
+    (dict(flags=8), -1),
+])
+def test_create_validates_descriptor(lib, kw, code):
+    h = ctypes.c_void_p()
+    d = _desc(**kw)
+    rc = lib.kwgb_create(ctypes.byref(d), ctypes.byref(h))
+    assert rc == code, lib.kwgb_last_error(None)
+    if rc == 0:
+        assert lib.kwgb_steps_done(h) == 0
+        assert lib.kwgb_device_bytes(h) == 0        # nothing allocated before set_medium
+        lib.kwgb_destroy(h)
+    else:
+        assert h.value is None
+        assert len(lib.kwgb_last_error(None)) > 0
+
+
+def test_state_errors_without_device(lib):
+    h = ctypes.c_void_p()
+    assert lib.kwgb_create(ctypes.byref(_desc()), ctypes.byref(h)) == 0
+    assert lib.kwgb_step(h, 1, None) == -6           # no medium yet
+    assert lib.kwgb_step(h, -1, None) == -1
+    assert b"n_steps" in lib.kwgb_last_error(h)
+    lib.kwgb_destroy(h)
+    lib.kwgb_destroy(None)

@@ -1,0 +1,181 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, element by element.
+
+Tolerances (float32 path vs float64 oracle, relative L2 / relative L-inf):
+  spectral operators (one FFT round trip)          1e-5 / 5e-5
+  config 1 (linear lossless, 200 steps)            1e-5 / 5e-5
+  heterogeneous nonlinear absorbing runs           1e-3 / 5e-3
+The float32 round trip of a 3D FFT carries about 1e-7 relative error per
+pass times log2(N); the long nonlinear runs accumulate it over hundreds of
+steps, which the 1e-3 bound covers with margin.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import linf, oracle_from_config, rel_l2
+from paper_1408_4675_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kw():
+    from paper_1408_4675_gb300 import build, kwgb
+    build.build()
+    kwgb.load()
+    return kwgb
+
+
+def _sim_for_ops(kw, shape, flags, y):
+    nz, ny, nx = shape
+    d = (1e-4, 1.25e-4, 0.8e-4)
+    sim = kw.Simulation(shape, d, 2e-8, 1500.0, flags=flags, alpha_power=y)
+    sim.set_medium(1500.0, 1000.0)
+    g = oracle.Grid(nx, ny, nz, *d, 2e-8, 1500.0, flags=flags, alpha_power=y)
+    return sim, g
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (16, 8, 32), (32, 64, 16), (64, 64, 64),
+                                   (8, 16, 1024), (1024, 8, 16), (16, 1024, 8)])
+@pytest.mark.parametrize("op", [0, 1, 2, 3])
+def test_spectral_operator_parity(kw, shape, op):
+    import torch
+    y = 1.3
+    sim, g = _sim_for_ops(kw, shape, kw.ABSORBING, y)
+    rng = np.random.default_rng(sum(shape) + op)
+    f = rng.standard_normal(shape).astype(np.float32)
+    dev = torch.from_numpy(f).cuda()
+    nout = 3 if op in (0, 1) else 1
+    outs = [torch.empty_like(dev) for _ in range(nout)]
+    sim.apply_operator(op, dev, outs)
+    torch.cuda.synchronize()
+    ref = oracle.apply_operator(g, op, f.astype(np.float64))
+    for got, r in zip(outs, ref):
+        got = got.cpu().numpy()
+        assert rel_l2(got, r) <= 1e-5, (shape, op, rel_l2(got, r))
+        assert linf(got, r) <= 5e-5, (shape, op, linf(got, r))
+    sim.close()
+
+
+def _run_both(kw, cfg, steps):
+    gsim, gids = kw.from_config(cfg)
+    osim, oids = oracle_from_config(cfg)
+    gsim.step(steps)
+    osim.step(steps)
+    return gsim, gids, osim, oids
+
+
+def _check_outputs(gsim, gids, osim, oids, cfg, tl2, tinf):
+    for (idx, rec), gi, oi in zip(cfg["sensors"], gids, oids):
+        for which in (kw_P_MAX, kw_P_RMS, kw_I_AVG):
+            if rec & which:
+                got = gsim.read(gi, which)
+                ref = osim.read(oi, which)
+                assert rel_l2(got, ref) <= tl2, (which, rel_l2(got, ref))
+                assert linf(got, ref) <= tinf, (which, linf(got, ref))
+
+
+kw_P_MAX, kw_P_RMS, kw_I_AVG = 1, 2, 4
+
+
+def _check_fields(gsim, osim, tl2, tinf, names=("p", "ux", "uy", "uz", "rhox", "rhoy", "rhoz")):
+    of = osim.fields()
+    for n in names:
+        got = gsim.read_field(n)
+        assert rel_l2(got, of[n]) <= tl2, (n, rel_l2(got, of[n]))
+        assert linf(got, of[n]) <= tinf, (n, linf(got, of[n]))
+
+
+def test_config1_linear_lossless_full(kw):
+    """64^3 water, Gaussian initial pressure, 200 steps, full-grid p_max."""
+    cfg = inputs.make_config(1)
+    gsim, gids, osim, oids = _run_both(kw, cfg, cfg["n_steps"])
+    _check_outputs(gsim, gids, osim, oids, cfg, 1e-5, 5e-5)
+    _check_fields(gsim, osim, 1e-4, 5e-4)
+    assert gsim.status() == 0
+    gsim.close()
+
+
+@pytest.mark.parametrize("n,steps", [(64, 120)])
+def test_config2_heterogeneous_nonlinear_absorbing(kw, n, steps):
+    cfg = inputs.make_config(2, n=n, n_steps=steps)
+    gsim, gids, osim, oids = _run_both(kw, cfg, steps)
+    _check_outputs(gsim, gids, osim, oids, cfg, 1e-3, 5e-3)
+    _check_fields(gsim, osim, 1e-3, 5e-3)
+    gsim.close()
+
+
+@pytest.mark.parametrize("n,steps", [(64, 150)])
+def test_config3_bowl_tissue_with_intensity(kw, n, steps):
+    cfg = inputs.make_config(3, n=n, n_steps=steps)
+    gsim, gids, osim, oids = _run_both(kw, cfg, steps)
+    _check_outputs(gsim, gids, osim, oids, cfg, 1e-3, 5e-3)
+    gsim.close()
+
+
+def test_config5_segmented_bowl_forward(kw):
+    cfg = inputs.make_config(5, n=64, n_steps=100)
+    gsim, gids, osim, oids = _run_both(kw, cfg, 100)
+    _check_outputs(gsim, gids, osim, oids, cfg, 1e-3, 5e-3)
+    gsim.close()
+
+
+def test_anisotropic_grid_every_feature(kw):
+    """Small anisotropic grid (ragged column tiles along x, every axis a
+    different size) with PML, heterogeneous nonlinear absorbing medium, an
+    initial pressure, overlapping sources and all sensor outputs."""
+    shape = (16, 8, 32)
+    cfg = inputs.make_config(2, n=16, n_steps=40)
+    nz, ny, nx = shape
+    rng = np.random.default_rng(5)
+    cfg["shape"] = shape
+    cfg["d"] = (1e-4, 0.9e-4, 1.1e-4)
+    for key, lo, hi in (("c0", 1450, 1650), ("rho0", 950, 1100), ("bona", 5, 9)):
+        cfg[key] = inputs.smooth_random_field(shape, lo, hi, int(rng.integers(1 << 30)), 2.0)
+    cfg["alpha0"] = inputs.db_to_neper(inputs.smooth_random_field(shape, 0.3, 1.0, 11, 2.0), 1.1)
+    cfg["c_ref"] = float(cfg["c0"].max())
+    cfg["dt"] = 0.3 * 0.9e-4 / cfg["c_ref"]
+    cfg["pml_size"] = (3, 2, 4)
+    cfg["p0"] = inputs.gaussian_ball(shape, 1.5, 2e5)
+    src = np.array([5, 40, 41, 300, 300, nx * ny * nz - 1])
+    cfg["sources"] = [(src, inputs.cw(1e6, 1e5, cfg["dt"], 30)),
+                      (np.array([40, 41]), np.stack([inputs.cw(1e6, 2e4, cfg["dt"], 40),
+                                                    inputs.tone_burst(1e6, 2, 3e4, cfg["dt"], 40)]))]
+    sens = np.array([0, 7, 40, 41, 333, 1000, nx * ny * nz - 1])
+    cfg["sensors"] = [(sens, 7), (None, 3), (np.array([41]), 1)]
+    gsim, gids, osim, oids = _run_both(kw, cfg, 40)
+    _check_outputs(gsim, gids, osim, oids, cfg, 1e-4, 5e-4)
+    _check_fields(gsim, osim, 1e-4, 5e-4)
+    gsim.close()
+
+
+def test_zero_steps_and_repeated_reads(kw):
+    cfg = inputs.make_config(3, n=32, n_steps=10)
+    gsim, gids = kw.from_config(cfg)
+    gsim.step(0)
+    assert np.all(np.isneginf(gsim.read(gids[0], kw_P_MAX)))
+    assert np.all(gsim.read(gids[0], kw_P_RMS) == 0)
+    gsim.step(5)
+    a = gsim.read(gids[0], kw_I_AVG)
+    b = gsim.read(gids[0], kw_I_AVG)          # the read-time tail changes no state
+    np.testing.assert_array_equal(a, b)
+    gsim.step(5)
+    osim, oids = oracle_from_config(cfg)
+    osim.step(10)
+    got, ref = gsim.read(gids[0], kw_I_AVG), osim.read(oids[0], kw_I_AVG)
+    assert rel_l2(got, ref) <= 1e-3
+    gsim.close()
+
+
+def test_two_runs_are_bitwise_identical(kw):
+    cfg = inputs.make_config(2, n=32, n_steps=20)
+    out = []
+    for _ in range(2):
+        gsim, gids = kw.from_config(cfg)
+        gsim.step(20)
+        out.append((gsim.read(gids[0], kw_P_MAX), gsim.read_field("p")))
+        gsim.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
