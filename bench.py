@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 k-space pseudospectral time step.
+
+Workload (default): the 512^3 HIFU case -- spherical bowl (R = 64 mm,
+aperture 60 mm) driving 1 MHz CW at 1.5 MPa through water into seeded layered
+soft tissue; nonlinear, power-law absorbing, every medium property a full
+field; sensors on a 65^3 focal box (p_max, p_rms, intensity) and the central
+xz-plane (p_max, p_rms).  ``--config 4`` runs the 1024^3 case instead.
+
+One step = one full time step (Eqs. 4a-4d, 6, 8: 14 FFT-equivalents, the
+fused updates, sources and sensors).  The metric is ms per step (lower is
+better), measured with CUDA events on the stream the library launches on,
+after warm-up; every field is larger than the 129 MB L2, so no flush is
+needed between steps.  The roofline object reports the dominant kernel's
+algorithmic bytes per launch over its event-timed duration against the
+measured HBM copy bandwidth.
+
+``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
+host cores instead, on a bounded sample of the same workload.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1408_4675_gb300 import inputs  # noqa: E402
+
+METRIC = "ms_per_step"
+UNIT = "ms/step"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=3, choices=[3, 4])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload_name(cfg):
+    n = cfg["shape"][0]
+    return "hifu_bowl_layered_tissue_%d^3" % n
+
+
+# ---------------------------------------------------------------- byte model
+def kernel_bytes(cfg):
+    """Algorithmic HBM bytes per launch of each kernel kind: every array the
+    kernel must read or write, counted once (spectra as the nx/2+1 complex
+    columns actually used; scalar medium properties take no bytes)."""
+    nz, ny, nx = cfg["shape"]
+    N = nx * ny * nz
+    S = (nx // 2 + 1) * 8 * ny * nz
+    F = 4 * N
+    fld = lambda k: 0 if np.isscalar(cfg[k]) or np.ndim(cfg[k]) == 0 else F
+    nonlinear = bool(cfg["flags"] & 1)
+    absorbing = bool(cfg["flags"] & 2)
+    nfull = sum(1 for idx, _ in cfg["sensors"] if idx is None)
+    full = nfull * 24 * N
+    b = {
+        "y_fwd_p": 2 * S, "z_grad": 4 * S, "y_inv_grad": 6 * S,
+        "x_vel": 6 * S + 6 * F + fld("rho0"),
+        "y_fwd_u": 6 * S, "z_div": 6 * S, "y_inv_div": 6 * S,
+    }
+    if absorbing:
+        b["x_dens"] = 5 * S + 7 * F + fld("rho0")
+        b.update({"y_fwd_abs": 4 * S, "z_abs": 4 * S, "y_inv_abs": 4 * S})
+        b["x_eos"] = 3 * S + F + fld("c0") + fld("alpha0") + (fld("rho0") + fld("bona") if nonlinear else 0) + full
+    else:
+        b["x_dens"] = 4 * S + 6 * F + fld("rho0") + fld("c0") + (fld("bona") if nonlinear else 0) + full
+    return b
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel, shape):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current sources."""
+    try:
+        from paper_1408_4675_gb300 import build
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t.get("%s@%d" % (kernel, shape[0]))
+        if e and e.get("source_digest") == build._digest():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+def oracle_sample(cfg_id, n_sample, steps):
+    """Time the FP64 oracle on the same recipe at n_sample^3; returns seconds
+    per step and the threads used."""
+    from oracle import kspace
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from helpers import oracle_from_config
+    cfg = inputs.make_config(cfg_id, n=n_sample, n_steps=max(steps, 1))
+    sim, _ = oracle_from_config(cfg)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    return (time.perf_counter() - t0) / steps, kspace.workers()
+
+
+def scale_to(n_from, n_to):
+    """Scale a per-step time by grid points times log2(grid points) (the 3D
+    FFTs dominate the oracle)."""
+    a, b = n_from ** 3, n_to ** 3
+    return (b * math.log2(b)) / (a * math.log2(a))
+
+
+# ---------------------------------------------------------------- arms
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    cfg = inputs.make_config(args.config, n_steps=1)
+    n_full = cfg["shape"][0]
+    n_s = 128
+    for _ in range(args.warmup):
+        oracle_sample(args.config, n_s, 1)
+    per = []
+    for _ in range(args.steps):
+        s, cores = oracle_sample(args.config, n_s, 1)
+        per.append(s)
+    ms = 1e3 * statistics.mean(per) * scale_to(n_s, n_full)
+    sample = "config-%d recipe on a %d^3 grid, 1 step per timed step, scaled to %d^3 by N log2 N" % (
+        args.config, n_s, n_full)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(ms, 3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(cfg), "grid": list(cfg["shape"])},
+        "cpu_baseline": {"value": round(ms, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(ms, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1408_4675_gb300 import build, kwgb
+    build.build()
+    kwgb.load()
+
+    cfg = inputs.make_config(args.config, n_steps=args.warmup + args.steps + 16)
+    stream = torch.cuda.current_stream()
+    sim, ids = kwgb.from_config(cfg)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    sim.step(args.warmup, stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    time.sleep(0.4)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = sim.launch_count
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = sim.launch_count - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # per-kernel durations from event-instrumented steps
+    prof = {}
+    for _ in range(min(5, max(args.steps, 1))):
+        for name, t in sim.step_profiled(stream):
+            prof.setdefault(name, []).append(t)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    status = sim.status()
+    sim.close()
+
+    kb = kernel_bytes(cfg)
+    steps_prof = min(5, max(args.steps, 1))
+    per_kernel = {k: sum(v) / steps_prof for k, v in prof.items()}
+    step_prof_ms = sum(per_kernel.values())
+    dom = max(per_kernel, key=per_kernel.get)
+    dom_ms = statistics.mean(prof[dom])
+    peak, peak_src = measured_peaks()
+    achieved = kb.get(dom, 0) / (dom_ms * 1e-3) / 1e9
+    step_bytes = sum(kb.get(k, 0) for k in per_kernel)
+    N = cfg["shape"][0] * cfg["shape"][1] * cfg["shape"][2]
+
+    out = {
+        "metric": METRIC, "value": round(ms, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(cfg), "grid": list(cfg["shape"]),
+                   "nonlinear": True, "absorbing": True, "heterogeneous": True,
+                   "l2": "every field (>= 537 MB) exceeds the 129 MB L2; no flush needed",
+                   "parallelism": "replicas" if world > 1 else "single_gpu"},
+        "grid_point_steps_per_s": round(world * N / (ms * 1e-3), 1),
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": ncu_traffic(dom, cfg["shape"]),
+                     "algorithmic_bytes_per_launch": kb.get(dom), "launch_ms": round(dom_ms, 4),
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
+        "step_roofline": {"bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (ms * 1e-3) / 1e9, 1),
+                          "frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4)},
+        "kernels_ms": {k: round(v, 4) for k, v in sorted(per_kernel.items(), key=lambda kv: -kv[1])},
+        "clocks": clk,
+        "device_status": status,
+    }
+
+    if not args.no_e2e:
+        out["e2e"] = e2e(args, cfg, kwgb, torch)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        s, cores = oracle_sample(args.config, 128, 6)
+        cpu_ms = 1e3 * s * scale_to(128, cfg["shape"][0])
+        out["cpu_baseline"] = {"value": round(cpu_ms, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "FP64 oracle, config-%d recipe on a 128^3 grid, 6 steps, "
+                                         "scaled to %d^3 by N log2 N" % (args.config, cfg["shape"][0])}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e(args, cfg, kwgb, torch):
+    """The same metric through the public API with host buffers: set-up from
+    pinned host arrays, K steps, and every sensor output read back, all inside
+    the timed region (wall clock, synchronised)."""
+    def pinned(a):
+        a = np.asarray(a, dtype=np.float32)
+        t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+    host = {k: (cfg[k] if np.ndim(cfg[k]) == 0 else pinned(cfg[k])) for k in ("c0", "rho0", "bona", "alpha0")}
+    h2d = sum(v.nbytes for v in host.values() if not np.isscalar(v) and np.ndim(v) > 0)
+    h2d += sum(idx.nbytes + 4 * np.size(sig) for idx, sig in cfg["sources"])
+    h2d += sum(idx.nbytes for idx, _ in cfg["sensors"] if idx is not None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = kwgb.Simulation(cfg["shape"], cfg["d"], cfg["dt"], cfg["c_ref"], cfg["pml_size"],
+                          cfg["pml_alpha"], cfg["flags"], cfg["alpha_power"])
+    sim.set_medium(host["c0"], host["rho0"], host["bona"], host["alpha0"])
+    for idx, sig in cfg["sources"]:
+        sim.add_source(idx, sig)
+    ids = [sim.add_sensor(idx, rec) for idx, rec in cfg["sensors"]]
+    sim.step(args.steps)
+    d2h = 0
+    for (idx, rec), i in zip(cfg["sensors"], ids):
+        for which in (1, 2, 4):
+            if rec & which:
+                d2h += sim.read(i, which).nbytes
+    t1 = time.perf_counter()
+    sim.close()
+    return {"value": round(1e3 * (t1 - t0) / args.steps, 4), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d // args.steps), "d2h_bytes_per_step": int(d2h // args.steps),
+            "what": "create + medium upload from pinned host memory + sources/sensors + %d steps + "
+                    "read of every sensor output, per step" % args.steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -183,6 +183,22 @@ int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float* out0,
 /* Number of steps taken so far. */
 int64_t kwgb_steps_done(const kwgb_sim* sim);
 
+/* Kernels launched by the simulation so far (all calls). */
+int64_t kwgb_launch_count(const kwgb_sim* sim);
+
+/* One time step like kwgb_step(sim, 1, cuda_stream), with a CUDA event
+ * recorded on cuda_stream after every kernel launch.  Synchronises.  Writes
+ * for each launch, in order, its kernel kind (see kwgb_kernel_name) to
+ * kinds[] and its device duration in milliseconds (from the previous event)
+ * to ms[], at most capacity entries; *n_launches receives the count.  This is
+ * the measurement hook of the benchmark.  Errors: ARG, STATE, CUDA. */
+int kwgb_step_profiled(kwgb_sim* sim, void* cuda_stream, int32_t* kinds, float* ms,
+                       int32_t capacity, int32_t* n_launches);
+
+/* Name of a kernel kind reported by kwgb_step_profiled ("" if unknown).
+ * The string is static. */
+const char* kwgb_kernel_name(int32_t kind);
+
 /* Synchronise and report device-side status: KWGB_OK, KWGB_ERR_NONFINITE
  * or KWGB_ERR_CUDA. */
 int kwgb_status(kwgb_sim* sim);

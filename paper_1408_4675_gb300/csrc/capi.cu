@@ -89,6 +89,11 @@ struct kwgb_sim {
     double* I_tail = nullptr;
     float* ubuf = nullptr;
     cudaStream_t last_stream = nullptr;
+    int64_t launches = 0;       // kernels launched so far
+    // per-launch event timing (kwgb_step_profiled)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int32_t> ev_kind;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -326,6 +331,30 @@ extern "C" int kwgb_set_medium(kwgb_sim* sim, const float* c0, const float* rho0
             return fail(sim, KWGB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+static const char* const kKernelNames[] = {
+    "y_fwd_p", "z_grad", "y_inv_grad", "x_vel", "y_fwd_u", "z_div", "y_inv_div", "x_dens",
+    "y_fwd_abs", "z_abs", "y_inv_abs", "x_eos", "intensity_gather", "intensity_accum", "advance_step"};
+enum { K_Y_FWD_P, K_Z_GRAD, K_Y_INV_GRAD, K_X_VEL, K_Y_FWD_U, K_Z_DIV, K_Y_INV_DIV, K_X_DENS,
+       K_Y_FWD_ABS, K_Z_ABS, K_Y_INV_ABS, K_X_EOS, K_I_GATHER, K_I_ACCUM, K_ADVANCE, K_COUNT };
+
+// Count a launch; when profiling, record an event after it on the launch stream.
+static int mark(kwgb_sim* sim, int kind, cudaStream_t s) {
+    sim->launches++;
+    if (!sim->prof) return KWGB_OK;
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(e, s));
+    sim->ev.push_back(e);
+    sim->ev_kind.push_back(kind);
+    return KWGB_OK;
+}
+
+#define LKM(call, kind)                                                                \
+    do {                                                                               \
+        LK(call);                                                                      \
+        if (int e2_ = mark(sim, kind, s)) return e2_;                                  \
+    } while (0)
+
 // spectrum -> gradient spectra (x still transformed): y fwd, z op, y inv
 static int grad_chain(kwgb_sim* sim, float2* in, float2* const out[3], int kind, cudaStream_t s) {
     const GridC& g = sim->g;
@@ -346,22 +375,22 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
     // Eq. 4a: y fwd of x-transformed p, z fwd + operator + z inv (3 outputs), y inv
     {
         float2* i1[1] = {sim->P};
-        LK(launch_y_pass(g, -1, i1, i1, 1, s));
+        LKM(launch_y_pass(g, -1, i1, i1, 1, s), K_Y_FWD_P);
         float2* zin[3] = {sim->P, nullptr, nullptr};
-        LK(launch_z_op(g, Z_GRAD_FWD, zin, sp, s));
-        LK(launch_y_pass(g, +1, sp, sp, 3, s));
+        LKM(launch_z_op(g, Z_GRAD_FWD, zin, sp, s), K_Z_GRAD);
+        LKM(launch_y_pass(g, +1, sp, sp, 3, s), K_Y_INV_GRAD);
     }
-    if (sim->n_i) LK(launch_intensity_gather(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, s));
+    if (sim->n_i) LKM(launch_intensity_gather(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, s), K_I_GATHER);
     // Eq. 4b (+ x R2C of u), Eq. 4c (y fwd, z fwd + operator + z inv, y inv)
     XVelArgs va{};
     for (int a = 0; a < 3; ++a) { va.G[a] = sp[a]; va.u[a] = sim->u[a]; va.U[a] = sp[a]; }
-    LK(launch_x_vel(g, sim->md, XV_STEP, va, s));
+    LKM(launch_x_vel(g, sim->md, XV_STEP, va, s), K_X_VEL);
     if (sim->n_i)
-        LK(launch_intensity_accum(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, sim->sens.p_sens,
-                                  sim->i_slot, sim->I, sim->d_step, 1, s));
-    LK(launch_y_pass(g, -1, sp, sp, 3, s));
-    LK(launch_z_op(g, Z_DIV, sp, sp, s));
-    LK(launch_y_pass(g, +1, sp, sp, 3, s));
+        LKM(launch_intensity_accum(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, sim->sens.p_sens,
+                                   sim->i_slot, sim->I, sim->d_step, 1, s), K_I_ACCUM);
+    LKM(launch_y_pass(g, -1, sp, sp, 3, s), K_Y_FWD_U);
+    LKM(launch_z_op(g, Z_DIV, sp, sp, s), K_Z_DIV);
+    LKM(launch_y_pass(g, +1, sp, sp, 3, s), K_Y_INV_DIV);
     // Eq. 4d + source; lossless: Eq. 6 + sensors + R2C of p here
     XDensArgs da{};
     for (int a = 0; a < 3; ++a) { da.D[a] = sp[a]; da.rho[a] = sim->rho[a]; }
@@ -370,19 +399,19 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
         da.S = sim->P;
         da.R = sim->T1;
         da.rho_tot = reinterpret_cast<float*>(sim->T2);
-        LK(launch_x_dens(g, sim->md, sim->src, sens, st, da, s));
+        LKM(launch_x_dens(g, sim->md, sim->src, sens, st, da, s), K_X_DENS);
         // Eq. 8: y fwd, z fwd + k^{y-2} / k^{y-1} + z inv, y inv, then Eq. 6
         float2* ab[3] = {sim->P, sim->T1, nullptr};
-        LK(launch_y_pass(g, -1, ab, ab, 2, s));
-        LK(launch_z_op(g, Z_ABS, ab, ab, s));
-        LK(launch_y_pass(g, +1, ab, ab, 2, s));
+        LKM(launch_y_pass(g, -1, ab, ab, 2, s), K_Y_FWD_ABS);
+        LKM(launch_z_op(g, Z_ABS, ab, ab, s), K_Z_ABS);
+        LKM(launch_y_pass(g, +1, ab, ab, 2, s), K_Y_INV_ABS);
         XEosArgs ea{sim->P, sim->T1, reinterpret_cast<float*>(sim->T2), sim->P};
-        LK(launch_x_eos(g, sim->md, sens, st, ea, s));
+        LKM(launch_x_eos(g, sim->md, sens, st, ea, s), K_X_EOS);
     } else {
         da.P = sim->P;
-        LK(launch_x_dens(g, sim->md, sim->src, sens, st, da, s));
+        LKM(launch_x_dens(g, sim->md, sim->src, sens, st, da, s), K_X_DENS);
     }
-    LK(launch_advance_step(sim->d_step, s));
+    LKM(launch_advance_step(sim->d_step, s), K_ADVANCE);
     return KWGB_OK;
 }
 
@@ -599,6 +628,53 @@ extern "C" int kwgb_step(kwgb_sim* sim, int64_t n_steps, void* cuda_stream) {
 }
 
 extern "C" int64_t kwgb_steps_done(const kwgb_sim* sim) { return sim ? sim->steps : 0; }
+
+extern "C" int64_t kwgb_launch_count(const kwgb_sim* sim) { return sim ? sim->launches : 0; }
+
+extern "C" const char* kwgb_kernel_name(int32_t kind) {
+    return (kind >= 0 && kind < K_COUNT) ? kKernelNames[kind] : "";
+}
+
+extern "C" int kwgb_step_profiled(kwgb_sim* sim, void* cuda_stream, int32_t* kinds, float* ms,
+                                  int32_t capacity, int32_t* n_launches) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (!kinds || !ms || !n_launches || capacity <= 0) return fail(sim, KWGB_ERR_ARG, "null output");
+    if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
+    if (int e = freeze(sim)) return e;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sim->last_stream = s;
+    cudaEvent_t start;
+    CK(cudaEventCreate(&start));
+    CK(cudaEventRecord(start, s));
+    sim->prof = true;
+    sim->ev.clear();
+    sim->ev_kind.clear();
+    int rc = launch_step(sim, s);
+    sim->prof = false;
+    if (rc == KWGB_OK) {
+        sim->steps++;
+        cudaError_t e = cudaEventSynchronize(sim->ev.empty() ? start : sim->ev.back());
+        if (e != cudaSuccess) rc = fail(sim, KWGB_ERR_CUDA, cudaGetErrorString(e));
+    }
+    int32_t n = 0;
+    cudaEvent_t prev = start;
+    for (size_t i = 0; i < sim->ev.size(); ++i) {
+        if (rc == KWGB_OK && n < capacity) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, prev, sim->ev[i]);
+            kinds[n] = sim->ev_kind[i];
+            ms[n] = t;
+            ++n;
+        }
+        prev = sim->ev[i];
+    }
+    for (cudaEvent_t e : sim->ev) cudaEventDestroy(e);
+    cudaEventDestroy(start);
+    sim->ev.clear();
+    sim->ev_kind.clear();
+    *n_launches = n;
+    return rc;
+}
 
 static int sync_and_flag(kwgb_sim* sim) {
     CK(cudaStreamSynchronize(sim->last_stream));

@@ -76,6 +76,12 @@ def load():
     L.kwgb_device_bytes.restype = i64
     L.kwgb_last_error.argtypes = [vp]
     L.kwgb_last_error.restype = ctypes.c_char_p
+    L.kwgb_launch_count.argtypes = [vp]
+    L.kwgb_launch_count.restype = i64
+    L.kwgb_step_profiled.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(i32)]
+    L.kwgb_step_profiled.restype = ctypes.c_int
+    L.kwgb_kernel_name.argtypes = [i32]
+    L.kwgb_kernel_name.restype = ctypes.c_char_p
     L.kwgb_destroy.argtypes = [vp]
     L.kwgb_destroy.restype = None
     for name in ("kwgb_create", "kwgb_set_allocator", "kwgb_set_medium", "kwgb_set_initial_pressure",
@@ -239,6 +245,20 @@ class Simulation:
         p = [ctypes.c_void_p(t.data_ptr()) for t in outs] + [None] * (3 - len(outs))
         self._check(self.L.kwgb_apply_operator(self.h, op, ctypes.c_void_p(field.data_ptr()),
                                                p[0], p[1], p[2], _stream_ptr(stream)))
+
+    @property
+    def launch_count(self):
+        return self.L.kwgb_launch_count(self.h)
+
+    def step_profiled(self, stream=None):
+        """One step with per-launch CUDA-event timing: [(kernel name, ms), ...]."""
+        cap = 64
+        kinds = np.zeros(cap, dtype=np.int32)
+        ms = np.zeros(cap, dtype=np.float32)
+        n = ctypes.c_int32()
+        self._check(self.L.kwgb_step_profiled(self.h, _stream_ptr(stream), _ptr(kinds), _ptr(ms),
+                                              cap, ctypes.byref(n)))
+        return [(self.L.kwgb_kernel_name(int(kinds[i])).decode(), float(ms[i])) for i in range(n.value)]
 
     def status(self):
         return self.L.kwgb_status(self.h)
