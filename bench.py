@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=3, choices=[3, 4])
+    ap.add_argument("--n", type=int, default=None,
+                    help="cubic grid size override (same recipe; for profiling small cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -193,7 +195,7 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
-    cfg = inputs.make_config(args.config, n_steps=1)
+    cfg = inputs.make_config(args.config, n=args.n, n_steps=1)
     n_full = cfg["shape"][0]
     n_s = 128
     for _ in range(args.warmup):
@@ -227,7 +229,7 @@ def run_ours(args):
     build.build()
     kwgb.load()
 
-    cfg = inputs.make_config(args.config, n_steps=args.warmup + args.steps + 16)
+    cfg = inputs.make_config(args.config, n=args.n, n_steps=args.warmup + args.steps + 16)
     stream = torch.cuda.current_stream()
     sim, ids = kwgb.from_config(cfg)
 

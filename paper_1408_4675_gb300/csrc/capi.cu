@@ -74,6 +74,7 @@ struct kwgb_sim {
     float2* T1 = nullptr;
     float2* T2 = nullptr;
     float2* T3 = nullptr;
+    SpecBuf bP{}, b1{}, b2{}, b3{};     // the same buffers with their TMA tensor maps
     int64_t* d_step = nullptr;
     int* d_flag = nullptr;
 
@@ -314,6 +315,16 @@ extern "C" int kwgb_set_medium(kwgb_sim* sim, const float* c0, const float* rho0
     DALLOC(sim->T2, float2, sim->spec_elems);
     DALLOC(sim->T3, float2, sim->spec_elems);
     CK(cudaMemset(sim->P, 0, sim->spec_elems * sizeof(float2)));
+    {
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
+        sim->g.num_sms = sms;
+        float2* bufs[4] = {sim->P, sim->T1, sim->T2, sim->T3};
+        SpecBuf* sb[4] = {&sim->bP, &sim->b1, &sim->b2, &sim->b3};
+        for (int i = 0; i < 4; ++i)
+            if (make_spec_maps(sim->g, bufs[i], sb[i]) != 0)
+                return fail(sim, KWGB_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    }
     DALLOC(sim->d_step, int64_t, 1);
     DALLOC(sim->d_flag, int, 1);
     CK(cudaMemset(sim->d_step, 0, sizeof(int64_t)));
@@ -355,14 +366,36 @@ static int mark(kwgb_sim* sim, int kind, cudaStream_t s) {
         if (int e2_ = mark(sim, kind, s)) return e2_;                                  \
     } while (0)
 
+// spectrum buffer -> its TMA descriptors
+static const SpecBuf* spec(kwgb_sim* sim, const float2* p) {
+    if (p == sim->P) return &sim->bP;
+    if (p == sim->T1) return &sim->b1;
+    if (p == sim->T2) return &sim->b2;
+    if (p == sim->T3) return &sim->b3;
+    return nullptr;
+}
+
+static cudaError_t ypass(kwgb_sim* sim, int dir, float2* const* in, float2* const* out, int n,
+                         cudaStream_t s) {
+    const SpecBuf* b[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < n; ++i) b[i] = spec(sim, in[i]);
+    return launch_y_pass(sim->g, dir, b, out, n, sim->d_flag, s);
+}
+
+static cudaError_t zop(kwgb_sim* sim, int kind, float2* const* in, float2* const* out, cudaStream_t s) {
+    const SpecBuf* b[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 3; ++i) b[i] = in[i] ? spec(sim, in[i]) : nullptr;
+    return launch_z_op(sim->g, kind, b, out, sim->d_flag, s);
+}
+
 // spectrum -> gradient spectra (x still transformed): y fwd, z op, y inv
 static int grad_chain(kwgb_sim* sim, float2* in, float2* const out[3], int kind, cudaStream_t s) {
     const GridC& g = sim->g;
     float2* i1[1] = {in};
-    LK(launch_y_pass(g, -1, i1, i1, 1, s));
+    LK(ypass(sim, -1, i1, i1, 1, s));
     float2* zin[3] = {in, nullptr, nullptr};
-    LK(launch_z_op(g, kind, zin, out, s));
-    LK(launch_y_pass(g, +1, out, out, 3, s));
+    LK(zop(sim, kind, zin, out, s));
+    LK(ypass(sim, +1, out, out, 3, s));
     return KWGB_OK;
 }
 
@@ -375,10 +408,10 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
     // Eq. 4a: y fwd of x-transformed p, z fwd + operator + z inv (3 outputs), y inv
     {
         float2* i1[1] = {sim->P};
-        LKM(launch_y_pass(g, -1, i1, i1, 1, s), K_Y_FWD_P);
+        LKM(ypass(sim, -1, i1, i1, 1, s), K_Y_FWD_P);
         float2* zin[3] = {sim->P, nullptr, nullptr};
-        LKM(launch_z_op(g, Z_GRAD_FWD, zin, sp, s), K_Z_GRAD);
-        LKM(launch_y_pass(g, +1, sp, sp, 3, s), K_Y_INV_GRAD);
+        LKM(zop(sim, Z_GRAD_FWD, zin, sp, s), K_Z_GRAD);
+        LKM(ypass(sim, +1, sp, sp, 3, s), K_Y_INV_GRAD);
     }
     if (sim->n_i) LKM(launch_intensity_gather(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, s), K_I_GATHER);
     // Eq. 4b (+ x R2C of u), Eq. 4c (y fwd, z fwd + operator + z inv, y inv)
@@ -388,9 +421,9 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
     if (sim->n_i)
         LKM(launch_intensity_accum(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, sim->sens.p_sens,
                                    sim->i_slot, sim->I, sim->d_step, 1, s), K_I_ACCUM);
-    LKM(launch_y_pass(g, -1, sp, sp, 3, s), K_Y_FWD_U);
-    LKM(launch_z_op(g, Z_DIV, sp, sp, s), K_Z_DIV);
-    LKM(launch_y_pass(g, +1, sp, sp, 3, s), K_Y_INV_DIV);
+    LKM(ypass(sim, -1, sp, sp, 3, s), K_Y_FWD_U);
+    LKM(zop(sim, Z_DIV, sp, sp, s), K_Z_DIV);
+    LKM(ypass(sim, +1, sp, sp, 3, s), K_Y_INV_DIV);
     // Eq. 4d + source; lossless: Eq. 6 + sensors + R2C of p here
     XDensArgs da{};
     for (int a = 0; a < 3; ++a) { da.D[a] = sp[a]; da.rho[a] = sim->rho[a]; }
@@ -402,9 +435,9 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
         LKM(launch_x_dens(g, sim->md, sim->src, sens, st, da, s), K_X_DENS);
         // Eq. 8: y fwd, z fwd + k^{y-2} / k^{y-1} + z inv, y inv, then Eq. 6
         float2* ab[3] = {sim->P, sim->T1, nullptr};
-        LKM(launch_y_pass(g, -1, ab, ab, 2, s), K_Y_FWD_ABS);
-        LKM(launch_z_op(g, Z_ABS, ab, ab, s), K_Z_ABS);
-        LKM(launch_y_pass(g, +1, ab, ab, 2, s), K_Y_INV_ABS);
+        LKM(ypass(sim, -1, ab, ab, 2, s), K_Y_FWD_ABS);
+        LKM(zop(sim, Z_ABS, ab, ab, s), K_Z_ABS);
+        LKM(ypass(sim, +1, ab, ab, 2, s), K_Y_INV_ABS);
         XEosArgs ea{sim->P, sim->T1, reinterpret_cast<float*>(sim->T2), sim->P};
         LKM(launch_x_eos(g, sim->md, sens, st, ea, s), K_X_EOS);
     } else {
@@ -681,6 +714,7 @@ static int sync_and_flag(kwgb_sim* sim) {
     CK(cudaDeviceSynchronize());
     int flag = 0;
     if (sim->d_flag) CK(cudaMemcpy(&flag, sim->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & 2) return fail(sim, KWGB_ERR_TIMEOUT, "a bounded device wait ran out (TMA tile load)");
     if (flag & 1) return fail(sim, KWGB_ERR_NONFINITE, "pressure became non-finite");
     return KWGB_OK;
 }
@@ -727,10 +761,10 @@ extern "C" int kwgb_read(kwgb_sim* sim, int32_t sensor_id, uint32_t which, doubl
         float2* out[3] = {sim->T3, sim->T1, sim->T2};
         float2* yi[1] = {sim->T3};
         float2* pin[1] = {sim->P};
-        LK(launch_y_pass(g, -1, pin, yi, 1, s));                  // out of place: P is kept
+        LK(ypass(sim, -1, pin, yi, 1, s));                  // out of place: P is kept
         float2* zin[3] = {sim->T3, nullptr, nullptr};
-        LK(launch_z_op(g, Z_GRAD_FWD, zin, out, s));
-        LK(launch_y_pass(g, +1, out, out, 3, s));
+        LK(zop(sim, Z_GRAD_FWD, zin, out, s));
+        LK(ypass(sim, +1, out, out, 3, s));
         XVelArgs va{};
         for (int a = 0; a < 3; ++a) {
             va.G[a] = out[a];
@@ -802,11 +836,11 @@ extern "C" int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float
     if (op == KWGB_OP_ABS_TAU || op == KWGB_OP_ABS_ETA) {
         LK(launch_x_r2c(g, in, g.nx, sim->T3, s));
         float2* a1[1] = {sim->T3};
-        LK(launch_y_pass(g, -1, a1, a1, 1, s));
+        LK(ypass(sim, -1, a1, a1, 1, s));
         float2* zin[3] = {nullptr, nullptr, nullptr};
         zin[op == KWGB_OP_ABS_TAU ? 0 : 1] = sim->T3;
-        LK(launch_z_op(g, Z_ABS, zin, zin, s));
-        LK(launch_y_pass(g, +1, a1, a1, 1, s));
+        LK(zop(sim, Z_ABS, zin, zin, s));
+        LK(ypass(sim, +1, a1, a1, 1, s));
         LK(launch_x_c2r(g, sim->T3, out0, g.nx, s));
         return KWGB_OK;
     }

@@ -54,22 +54,30 @@ __device__ __forceinline__ float2 rot16(float2 d, int m) {
 }
 
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+// Bit reversal of the low `bits` (<= 4) bits of i, written without recursion
+// so that it folds to a constant once the calling loop is unrolled.
 __host__ __device__ constexpr int bitrev(int i, int bits) {
-    return bits == 0 ? 0 : (((i & 1) << (bits - 1)) | bitrev(i >> 1, bits - 1));
+    return (((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3)) >> (4 - bits);
 }
 
 // In-register DFT of size R (2, 4, 8 or 16):
 //   v[k] <- sum_r v[r] exp(DIR 2 pi i r k / R)
 // as radix-2 decimation in frequency followed by a compile-time bit reversal.
+// Every loop has a compile-time trip count (the stage loop runs over the
+// stage index, not over a shifted span) so that it unrolls completely and
+// the array stays in registers.
 template <int R, int DIR>
 __device__ __forceinline__ void dft_reg(float2* v) {
     static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16, "radix");
+    constexpr int LR = ilog2c(R);
 #pragma unroll
-    for (int span = R / 2; span >= 1; span >>= 1) {
+    for (int st = 0; st < LR; ++st) {
+        const int span = R >> (st + 1);
 #pragma unroll
-        for (int start = 0; start < R; start += 2 * span) {
+        for (int g = 0; g < (1 << st); ++g) {
 #pragma unroll
-            for (int j = 0; j < span; ++j) {
+            for (int j = 0; j < (R >> (st + 1)); ++j) {
+                const int start = g * 2 * span;
                 const float2 a = v[start + j], b = v[start + j + span];
                 v[start + j] = cadd(a, b);
                 v[start + j + span] = rot16<DIR>(csub(a, b), j * (16 / (2 * span)));
@@ -79,7 +87,7 @@ __device__ __forceinline__ void dft_reg(float2* v) {
     if (R > 2) {
         float2 t[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) t[i] = v[bitrev(i, ilog2c(R))];
+        for (int i = 0; i < R; ++i) t[i] = v[bitrev(i, LR)];
 #pragma unroll
         for (int i = 0; i < R; ++i) v[i] = t[i];
     }

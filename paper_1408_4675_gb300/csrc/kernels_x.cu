@@ -15,8 +15,10 @@
 // A row of nx reals is treated as M = nx/2 complex values z[n] = x[2n] +
 // i x[2n+1]; an M-point FFT plus one post-processing step pairing bins k and
 // M-k gives the nx/2+1 bins of the real transform (and the reverse for C2R).
-// TL = M/E threads own a row; thread j holds z[j + TL*m], i.e. the float2 at
-// x = 2(j + TL*m), so every global access of a row is coalesced.
+// TL = M/E <= 32 threads own a row; thread j holds z[j + TL*m], i.e. the
+// float2 at x = 2(j + TL*m), so every global access of a row is coalesced.
+// A row never straddles a warp, so all synchronisation is warp-level and the
+// warps of a CTA stream their rows independently.
 #include "fft_core.cuh"
 #include "kwgb_internal.h"
 
@@ -29,6 +31,7 @@ struct XShape {
     static constexpr int M = 1 << LOGM;
     static constexpr int E = M >= 512 ? 16 : (M >= 8 ? 8 : M);
     static constexpr int TL = M / E;
+    static_assert(TL <= 32, "a row must fit in one warp");
     static constexpr int RPB = XTHREADS / TL;        // rows per CTA
     static constexpr int PITCH = M + M / 16 + 2;     // complex slots per row (padded, + Nyquist)
     static constexpr int SMEM = RPB * PITCH * (int)sizeof(float2);
@@ -38,7 +41,7 @@ struct RowSmem {
     float2* base;
     __device__ __forceinline__ float2& at(int e) { return base[e + (e >> 4)]; }
     __device__ __forceinline__ float& f(int x) { return reinterpret_cast<float*>(base)[x]; }
-    __device__ __forceinline__ void sync() { __syncthreads(); }
+    __device__ __forceinline__ void sync() { __syncwarp(); }
 };
 
 // Unnormalised C2R of one row: spec[0..M] (Hermitian half spectrum) ->
@@ -50,11 +53,11 @@ __device__ __forceinline__ void row_c2r(const float2* __restrict__ spec, RowSmem
                                         float2 (&z)[XShape<LOGM>::E]) {
     using Sh = XShape<LOGM>;
     constexpr int M = Sh::M, E = Sh::E, TL = Sh::TL;
-    __syncthreads();                                  // smem row free
+    __syncwarp();                                  // smem row free
     if (valid) {
         for (int k = j; k <= M; k += TL) S.at(k) = __ldcs(spec + k);
     }
-    __syncthreads();
+    __syncwarp();
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = j + TL * m;
@@ -74,10 +77,10 @@ __device__ __forceinline__ void row_r2c(float2 (&z)[XShape<LOGM>::E], RowSmem& S
     using Sh = XShape<LOGM>;
     constexpr int M = Sh::M, E = Sh::E, TL = Sh::TL;
     line_fft<LOGM, E, -1>(z, j, S, tw);
-    __syncthreads();
+    __syncwarp();
 #pragma unroll
     for (int m = 0; m < E; ++m) S.at(j + TL * m) = z[m];
-    __syncthreads();
+    __syncwarp();
     if (valid) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -134,14 +137,14 @@ __device__ __forceinline__ void finish_pressure(float2 (&p)[XShape<LOGM>::E], co
         }
     }
     if (sens.row_ptr) {                               // uniform over the launch
-        __syncthreads();
+        __syncwarp();
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int x = 2 * (j + TL * m);
             S.f(x) = p[m].x;
             S.f(x + 1) = p[m].y;
         }
-        __syncthreads();
+        __syncwarp();
         if (valid) {
             const int e0 = __ldg(sens.row_ptr + row), e1 = __ldg(sens.row_ptr + row + 1);
             for (int e = e0 + j; e < e1; e += TL) {
@@ -164,7 +167,7 @@ struct XVelK {
 };
 
 template <int LOGM, int MODE>
-__global__ void __launch_bounds__(XTHREADS) x_vel_kernel(const XVelK K) {
+__global__ void __launch_bounds__(XTHREADS, 2) x_vel_kernel(const XVelK K) {
     using Sh = XShape<LOGM>;
     constexpr int E = Sh::E, TL = Sh::TL;
     extern __shared__ float2 smem[];
@@ -180,44 +183,44 @@ __global__ void __launch_bounds__(XTHREADS) x_vel_kernel(const XVelK K) {
     const float* rho0 = K.md.rho0;
     const float rho0s = K.md.rho0_s;
 
+    float2 r0[E];                                     // rho0 of this row (x = 2n, 2n+1)
+#pragma unroll
+    for (int m = 0; m < E; ++m) r0[m] = rho0 ? ldg2(rho0 + rb + 2 * (j + TL * m)) : make_float2(rho0s, rho0s);
 #pragma unroll 1
     for (int xi = 0; xi < 3; ++xi) {
-        float2 v[E];
-        row_c2r<LOGM>(K.a.G[xi] + (size_t)rr * g.nhp, S, j, valid, g.t.tw, v);
-        // staggered-grid density (mean of the two neighbours along xi) and PML factor
+        // issue this component's field loads before the row transform
         size_t nb;                                    // row base of the +1 neighbour along y / z
         if (xi == 1) nb = (size_t)(((y + 1) & (g.ny - 1)) + g.ny * z) * g.nx;
         else nb = (size_t)(y + g.ny * ((z + 1) & (g.nz - 1))) * g.nx;
+        float2 uo[E], r1[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int x = 2 * (j + TL * m);
+            uo[m] = (MODE != XV_INIT && valid) ? ld2(K.a.u[xi] + rb + x) : make_float2(0.f, 0.f);
+            if (!rho0) r1[m] = make_float2(rho0s, rho0s);
+            else if (xi == 0) r1[m] = make_float2(__ldg(rho0 + rb + ((x + 2) & (g.nx - 1))), 0.f);
+            else r1[m] = ldg2(rho0 + nb + x);
+        }
+        float2 v[E];
+        row_c2r<LOGM>(K.a.G[xi] + (size_t)rr * g.nhp, S, j, valid, g.t.tw, v);
         const float fyz = xi == 1 ? __ldg(g.t.pml_sg[1] + y) : __ldg(g.t.pml_sg[2] + z);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int x = 2 * (j + TL * m);
+            // staggered-grid density: mean of the two neighbours along xi
             float2 rs;
-            if (rho0) {
-                const float2 r0 = ldg2(rho0 + rb + x);
-                if (xi == 0) {
-                    const float r2 = __ldg(rho0 + rb + ((x + 2) & (g.nx - 1)));
-                    rs = make_float2(0.5f * (r0.x + r0.y), 0.5f * (r0.y + r2));
-                } else {
-                    const float2 r1 = ldg2(rho0 + nb + x);
-                    rs = make_float2(0.5f * (r0.x + r1.x), 0.5f * (r0.y + r1.y));
-                }
-            } else {
-                rs = make_float2(rho0s, rho0s);
-            }
-            float2 f;
-            if (xi == 0) f = ldg2(g.t.pml_sg[0] + x);
-            else f = make_float2(fyz, fyz);
+            if (xi == 0) rs = make_float2(0.5f * (r0[m].x + r0[m].y), 0.5f * (r0[m].y + (rho0 ? r1[m].x : rho0s)));
+            else rs = make_float2(0.5f * (r0[m].x + r1[m].x), 0.5f * (r0[m].y + r1[m].y));
+            const float2 f = xi == 0 ? ldg2(g.t.pml_sg[0] + x) : make_float2(fyz, fyz);
             const float2 gr = v[m];
             float2 un;
             if (MODE == XV_INIT) {
                 // u^{-1/2} = +dt / (2 rho0_sg) d/dxi p0
                 un = make_float2(0.5f * g.dt * gr.x / rs.x, 0.5f * g.dt * gr.y / rs.y);
             } else {
-                const float2 uo = valid ? ld2(K.a.u[xi] + rb + x) : make_float2(0.f, 0.f);
                 // Eq. 4b with the PML: u <- f (f u - dt grad p / rho0_sg)
-                un = make_float2(f.x * (f.x * uo.x - g.dt * gr.x / rs.x),
-                                 f.y * (f.y * uo.y - g.dt * gr.y / rs.y));
+                un = make_float2(f.x * (f.x * uo[m].x - g.dt * gr.x / rs.x),
+                                 f.y * (f.y * uo[m].y - g.dt * gr.y / rs.y));
             }
             if (valid) {
                 if (MODE == XV_TAIL) st2(K.a.tail[xi] + (size_t)rr * 2 * g.nhp + x, un);
@@ -240,7 +243,7 @@ struct XDensK {
 };
 
 template <int LOGM, bool FUSED_EOS>
-__global__ void __launch_bounds__(XTHREADS) x_dens_kernel(const XDensK K) {
+__global__ void __launch_bounds__(XTHREADS, 2) x_dens_kernel(const XDensK K) {
     using Sh = XShape<LOGM>;
     constexpr int E = Sh::E, TL = Sh::TL;
     extern __shared__ float2 smem[];
@@ -263,11 +266,11 @@ __global__ void __launch_bounds__(XTHREADS) x_dens_kernel(const XDensK K) {
         const int p0 = valid ? __ldg(K.src.row_ptr + rr) : 0;
         const int p1 = valid ? __ldg(K.src.row_ptr + rr + 1) : 0;
         const int64_t n = *K.st.step;
-        __syncthreads();
+        __syncwarp();
         if (p1 > p0) {
             for (int x = j; x < g.nx; x += TL) S.f(x) = 0.f;
         }
-        __syncthreads();
+        __syncwarp();
         for (int p = p0 + j; p < p1; p += TL) {
             const int c0 = __ldg(K.src.pt_c + p), c1 = __ldg(K.src.pt_c + p + 1);
             float acc = 0.f;
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(XTHREADS) x_dens_kernel(const XDensK K) {
             const float c = md.c0 ? __ldg(md.c0 + rb + x) : md.c0_s;
             S.f(x) = acc / c;                          // dt * 2 s / (3 c0 dx)
         }
-        __syncthreads();
+        __syncwarp();
         if (p1 > p0) {
 #pragma unroll
             for (int m = 0; m < E; ++m) {
@@ -299,12 +302,16 @@ __global__ void __launch_bounds__(XTHREADS) x_dens_kernel(const XDensK K) {
     const float fy = __ldg(g.t.pml[1] + y), fz = __ldg(g.t.pml[2] + z);
 #pragma unroll 1
     for (int xi = 0; xi < 3; ++xi) {
+        float2 ro_[E];                                // issued before the row transform
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            ro_[m] = valid ? ld2(K.a.rho[xi] + rb + 2 * (j + TL * m)) : make_float2(0.f, 0.f);
         float2 d[E];
         row_c2r<LOGM>(K.a.D[xi] + (size_t)rr * g.nhp, S, j, valid, g.t.tw, d);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int x = 2 * (j + TL * m);
-            const float2 ro = valid ? ld2(K.a.rho[xi] + rb + x) : make_float2(0.f, 0.f);
+            const float2 ro = ro_[m];
             const float2 f = xi == 0 ? ldg2(g.t.pml[0] + x) : (xi == 1 ? make_float2(fy, fy) : make_float2(fz, fz));
             // Eq. 4d with the PML: rho_xi <- f (f rho_xi - dt rho0 d) / (1 + 2 dt d)
             float nx_ = f.x * (f.x * ro.x - g.dt * r0[m].x * d[m].x);
@@ -356,7 +363,7 @@ struct XEosK {
 };
 
 template <int LOGM>
-__global__ void __launch_bounds__(XTHREADS) x_eos_kernel(const XEosK K) {
+__global__ void __launch_bounds__(XTHREADS, 2) x_eos_kernel(const XEosK K) {
     using Sh = XShape<LOGM>;
     constexpr int E = Sh::E, TL = Sh::TL;
     extern __shared__ float2 smem[];
@@ -369,10 +376,13 @@ __global__ void __launch_bounds__(XTHREADS) x_eos_kernel(const XEosK K) {
     const int rr = valid ? row : 0;
     RowSmem S{smem + r * Sh::PITCH};
     const size_t rb = (size_t)rr * g.nx;
-    float2 a1[E], a2[E];
-    row_c2r<LOGM>(K.a.A1 + (size_t)rr * g.nhp, S, j, valid, g.t.tw, a1);
-    row_c2r<LOGM>(K.a.A2 + (size_t)rr * g.nhp, S, j, valid, g.t.tw, a2);
-    float2 p[E];
+    // Eq. 6 with Eq. 8 and Eq. 3:
+    //   p = c0^2 (rho + B/2A rho^2/rho0) + c0^2 tau a1 - c0^2 eta a2,
+    //   a1 = IFT{k^{y-2} FT{rho0 sum d}}, a2 = IFT{k^{y-1} FT{rho}},
+    //   tau = -2 alpha0 c0^{y-1}, eta = 2 alpha0 c0^y tan(pi y / 2).
+    // The local part and the two coefficients are formed before the two
+    // row transforms so that the field loads overlap them.
+    float2 p0[E], ct[E], ce[E];
     const float ym1 = md.y - 1.0f;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -381,30 +391,30 @@ __global__ void __launch_bounds__(XTHREADS) x_eos_kernel(const XEosK K) {
         const float2 rho = valid ? ld2(K.a.rho_tot + (size_t)rr * 2 * g.nhp + x) : make_float2(0.f, 0.f);
         const float2 c = med2(md.c0, md.c0_s, i);
         const float2 al = med2(md.alpha0, md.alpha0_s, i);
-        float pv[2];
-        const float cc[2] = {c.x, c.y}, aa[2] = {al.x, al.y}, rr2[2] = {rho.x, rho.y};
-        const float t1[2] = {a1[m].x, a1[m].y}, t2[2] = {a2[m].x, a2[m].y};
-        float2 r0 = make_float2(1.f, 1.f), ba = make_float2(0.f, 0.f);
+        float2 q = rho;
         if (md.nonlinear) {
-            r0 = med2(md.rho0, md.rho0_s, i);
-            ba = med2(md.bona, md.bona_s, i);
+            const float2 r0 = med2(md.rho0, md.rho0_s, i);
+            const float2 ba = med2(md.bona, md.bona_s, i);
+            q.x += 0.5f * ba.x * rho.x * rho.x / r0.x;
+            q.y += 0.5f * ba.y * rho.y * rho.y / r0.y;
         }
-        const float r0a[2] = {r0.x, r0.y}, baa[2] = {ba.x, ba.y};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            // Eq. 3: tau = -2 alpha0 c0^{y-1}, eta = 2 alpha0 c0^y tan(pi y / 2)
-            const float cy1 = exp2f(ym1 * log2f(cc[h]));
-            const float tau = -2.0f * aa[h] * cy1;
-            const float eta = 2.0f * aa[h] * cy1 * cc[h] * md.tan_pi_y_2;
-            // Eq. 8: L_d = -tau IFT{k^{y-2} FT{rho0 sum d}} + eta IFT{k^{y-1} FT{rho}}
-            const float ld = -tau * t1[h] + eta * t2[h];
-            float q = rr2[h];
-            if (md.nonlinear) q += 0.5f * baa[h] * rr2[h] * rr2[h] / r0a[h];
-            pv[h] = cc[h] * cc[h] * (q - ld);                               // Eq. 6
-        }
-        p[m] = make_float2(pv[0], pv[1]);
+        const float cx2 = c.x * c.x, cy2 = c.y * c.y;
+        const float px = exp2f(ym1 * log2f(c.x)), py = exp2f(ym1 * log2f(c.y));   // c0^{y-1}
+        p0[m] = make_float2(cx2 * q.x, cy2 * q.y);
+        ct[m] = make_float2(cx2 * (-2.0f * al.x * px), cy2 * (-2.0f * al.y * py));                 // c0^2 tau
+        ce[m] = make_float2(-cx2 * 2.0f * al.x * px * c.x * md.tan_pi_y_2,
+                            -cy2 * 2.0f * al.y * py * c.y * md.tan_pi_y_2);                        // -c0^2 eta
     }
-    finish_pressure<LOGM>(p, g, K.sens, K.st, S, j, valid, rr, K.a.P);
+    float2 a[E];
+    row_c2r<LOGM>(K.a.A1 + (size_t)rr * g.nhp, S, j, valid, g.t.tw, a);
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+        p0[m] = make_float2(fmaf(ct[m].x, a[m].x, p0[m].x), fmaf(ct[m].y, a[m].y, p0[m].y));
+    row_c2r<LOGM>(K.a.A2 + (size_t)rr * g.nhp, S, j, valid, g.t.tw, a);
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+        p0[m] = make_float2(fmaf(ce[m].x, a[m].x, p0[m].x), fmaf(ce[m].y, a[m].y, p0[m].y));
+    finish_pressure<LOGM>(p0, g, K.sens, K.st, S, j, valid, rr, K.a.P);
 }
 
 // ---------------------------------------------------------------- plain x

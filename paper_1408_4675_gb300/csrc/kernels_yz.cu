@@ -1,75 +1,61 @@
 // Strided-axis FFT passes on the half spectra [nz][ny][nhp] (complex64).
 //
-// A CTA owns a tile of CX consecutive x-columns times one whole line along
-// y (y pass) or z (z pass).  Thread (c, j) loads elements j + TL*m of column c
-// straight into registers: a warp reads 2 (CX = 16) or 4 (CX = 8) full
-// 64..128-byte row segments per instruction, so the strided axis is read with
-// coalesced accesses and each element crosses HBM once per pass.
+// Work item = a tile of CX consecutive x-columns times one whole line along
+// y (y pass) or z (z pass).  The kernels are persistent: each CTA walks its
+// share of the tiles with a two-stage shared-memory ring that the TMA unit
+// fills (cp.async.bulk.tensor, box CX x 256 lines, completion on an
+// mbarrier), so the HBM reads of tile t+1 run while tile t is transformed.
+// The x extent of the tensor map is nh (not the padded pitch), so the ragged
+// last tile reads no padding: the TMA zero-fills those columns.
+//
+// Thread (c, j) takes elements j + TL*m of column c into registers; the
+// Stockham passes exchange through the stage buffer the tile arrived in, and
+// results are stored from registers (a warp writes whole 64..128-byte row
+// segments).
 //
 // The z pass is the fused spectral-operator pass: forward z FFT, the
-// pointwise operator of Eq. 4a, 4c or 8 (which needs kx, ky, kz, all known
-// here), inverse z FFT, store.  It plays the role of the paper's
-// "transposed-space" spectral multiply (Sec. 3.2): the spectrum never
-// returns to HBM between the forward and the inverse transform along z.
+// pointwise operator of Eq. 4a, 4c or 8 (all of kx, ky, kz are known here),
+// inverse z FFT, store.  It plays the role of the paper's transposed-space
+// spectral multiply (Sec. 3.2): the spectrum does not return to HBM between
+// the forward and the inverse transform along z.
 #include "fft_core.cuh"
 #include "kwgb_internal.h"
+#include "tma.cuh"
 
 namespace kwgb {
 
+enum { OP_Y_FWD = 0, OP_Y_INV = 1, OP_Z_GRAD_FWD = 2, OP_Z_GRAD_BWD = 3, OP_Z_DIV = 4, OP_Z_ABS = 5 };
+
 template <int CX>
-struct ColSmem {
-    static constexpr int CXP = CX < 16 ? CX + 1 : CX;   // odd pitch for narrow tiles (banks)
+struct TileSmem {
     float2* buf;
     int c;
-    __device__ __forceinline__ float2& at(int e) { return buf[e * CXP + c]; }
+    __device__ __forceinline__ float2& at(int e) { return buf[e * CX + c]; }
     __device__ __forceinline__ void sync() { __syncthreads(); }
 };
 
-template <int LOGN>
-struct YZShape {
+template <int LOGN, bool ISY>
+struct TShape {
     static constexpr int N = 1 << LOGN;
-    static constexpr int E = LOGN >= 8 ? 16 : (N >= 8 ? 8 : N);
+    static constexpr int E = ISY ? (LOGN >= 8 ? 16 : 8) : 8;   // z: E = 8 keeps the operator pass spill-free
     static constexpr int TL = N / E;
-    static constexpr int CX = (512 / TL) >= 16 ? 16 : (512 / TL);
+    static constexpr int MAXT = 512;
+    static constexpr int CX = (MAXT / TL) >= 16 ? 16 : (MAXT / TL);
     static constexpr int THREADS = CX * TL;
-    static constexpr int SMEM = N * ColSmem<CX>::CXP * (int)sizeof(float2);
+    static constexpr int BOX = N < 256 ? N : 256;
+    static constexpr int NBOX = N / BOX;
+    static constexpr int STAGE = N * CX;                       // complex elements per stage
+    static constexpr int SMEM = 2 * STAGE * (int)sizeof(float2) + 64;
 };
 
-struct YArgs {
+struct alignas(64) YZK {
+    CUtensorMap map[3];       // input tensor maps (box of the pass)
     GridC g;
-    float2* in[3];
     float2* out[3];
-};
-
-template <int LOGN, int DIR>
-__global__ void __launch_bounds__(YZShape<LOGN>::THREADS)
-y_pass_kernel(const YArgs a) {
-    using Sh = YZShape<LOGN>;
-    constexpr int E = Sh::E, TL = Sh::TL, CX = Sh::CX;
-    extern __shared__ float2 smem[];
-    const int c = threadIdx.x % CX, j = threadIdx.x / CX;
-    const int col = blockIdx.x * CX + c;
-    const bool valid = col < a.g.nh;
-    const size_t off = (size_t)blockIdx.y * a.g.ny * a.g.nhp + col;
-    const size_t es = a.g.nhp;
-    const float2* __restrict__ in = a.in[blockIdx.z] + off;
-    float2* __restrict__ out = a.out[blockIdx.z] + off;
-    float2 v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m)
-        v[m] = valid ? __ldcs(in + (size_t)(j + TL * m) * es) : make_float2(0.f, 0.f);
-    ColSmem<CX> S{smem, c};
-    line_fft<LOGN, E, DIR>(v, j, S, a.g.t.tw);
-    if (valid) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
-    }
-}
-
-struct ZArgs {
-    GridC g;
-    float2* in[3];
-    float2* out[3];
+    int ncomp;                // y pass: components (items carry the component)
+    int nloads;               // z pass: loads per item
+    int load_comp[3];         // z pass: component of each load
+    int* flag;
 };
 
 // sinc(x) = sin(x)/x with sinc(0) = 1 (kappa of Sec. 2.2)
@@ -78,182 +64,299 @@ __device__ __forceinline__ float sinc_f(float x) {
 }
 
 template <int LOGN, int OP>
-__global__ void __launch_bounds__(YZShape<LOGN>::THREADS)
-z_op_kernel(const ZArgs a) {
-    using Sh = YZShape<LOGN>;
-    constexpr int E = Sh::E, TL = Sh::TL, CX = Sh::CX;
-    extern __shared__ float2 smem[];
+__global__ void __launch_bounds__(TShape<LOGN, (OP < 2)>::THREADS, 1)
+yz_kernel(const __grid_constant__ YZK a) {
+    constexpr bool ISY = OP < 2;
+    using Sh = TShape<LOGN, ISY>;
+    constexpr int E = Sh::E, TL = Sh::TL, CX = Sh::CX, STAGE = Sh::STAGE;
+    extern __shared__ __align__(128) float2 smem[];
+    __shared__ int abort_flag;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
     const GridC& g = a.g;
-    const int c = threadIdx.x % CX, j = threadIdx.x / CX;
-    const int col = blockIdx.x * CX + c;
-    const int y = blockIdx.y;
-    const bool valid = col < g.nh;
-    const size_t off = (size_t)y * g.nhp + col;
-    const size_t es = (size_t)g.ny * g.nhp;
-    ColSmem<CX> S{smem, c};
+    const int tid = threadIdx.x;
+    const int c = tid % CX, j = tid / CX;
+    const int nchunk = (g.nh + CX - 1) / CX;
+    const int lines = ISY ? g.nz : g.ny;
+    const int items = nchunk * lines * (ISY ? a.ncomp : 1);
+    const int L = ISY ? 1 : a.nloads;
+    const int my = items > (int)blockIdx.x ? (items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int Q = my * L;
 
-    const float kx = valid ? __ldg(g.t.kx + col) : 0.f;
-    const float ky = __ldg(g.t.ky + y);
-    float k2[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-        const float kz = __ldg(g.t.kz + j + TL * m);
-        k2[m] = fmaf(kx, kx, fmaf(ky, ky, kz * kz));
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        abort_flag = 0;
     }
+    __syncthreads();
 
-    if (OP == Z_GRAD_FWD || OP == Z_GRAD_BWD) {
+    auto issue = [&](int q) {                 // thread 0 only
+        const int item = (int)blockIdx.x + (q / L) * (int)gridDim.x;
+        const int l = q % L;
+        const int chunk = item % nchunk;
+        const int line = (item / nchunk) % lines;
+        const int mi = ISY ? item / (nchunk * lines) : a.load_comp[l];
+        const CUtensorMap* map = &a.map[mi];
+        float2* dst = smem + (q & 1) * STAGE;
+        uint64_t* b = &bar[q & 1];
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(b, STAGE * (uint32_t)sizeof(float2));
+#pragma unroll
+        for (int k = 0; k < Sh::NBOX; ++k) {
+            if (ISY) tma_load_3d(dst + k * Sh::BOX * CX, map, chunk * CX, k * Sh::BOX, line, b);
+            else tma_load_3d(dst + k * Sh::BOX * CX, map, chunk * CX, line, k * Sh::BOX, b);
+        }
+    };
+
+    if (tid == 0 && Q > 0) issue(0);
+    float kap[E];
+    float lg[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) { kap[m] = 0.f; lg[m] = 0.f; }
+
+    for (int q = 0; q < Q; ++q) {
+        const int s = q & 1;
+        if (tid == 0 && q + 1 < Q) issue(q + 1);
+        const bool ok = mbar_wait_bounded(&bar[s], (q >> 1) & 1, a.flag);
+        if (!ok) abort_flag = 1;
+        const int item = (int)blockIdx.x + (q / L) * (int)gridDim.x;
+        const int l = q % L;
+        const int chunk = item % nchunk;
+        const int line = (item / nchunk) % lines;
+        const int col = chunk * CX + c;
+        const bool valid = ok && col < g.nh;
+        TileSmem<CX> S{smem + s * STAGE, c};
         float2 v[E];
-        const float2* __restrict__ in = a.in[0] + off;
 #pragma unroll
-        for (int m = 0; m < E; ++m)
-            v[m] = valid ? __ldcs(in + (size_t)(j + TL * m) * es) : make_float2(0.f, 0.f);
-        line_fft<LOGN, E, -1>(v, j, S, g.t.tw);
-        float kap[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) kap[m] = sinc_f(g.hk * sqrtf(k2[m])) * g.scale;
-        const float2 dx = valid ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
-        const float2 dy = __ldg(g.t.dfy + y);
-#pragma unroll 1
-        for (int xi = 0; xi < 3; ++xi) {
-            float2* __restrict__ out = a.out[xi];
-            if (out == nullptr) continue;          // uniform across the CTA
-            out += off;
-            float2 w[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
-                if (OP == Z_GRAD_BWD) d = make_float2(-d.x, d.y);   // i k e^{-ikd/2} = -conj(i k e^{+ikd/2})
-                w[m] = cscale(cmul(v[m], d), kap[m]);
-            }
-            line_fft<LOGN, E, +1>(w, j, S, g.t.tw);
+        for (int m = 0; m < E; ++m) v[m] = S.at(j + TL * m);
+
+        if (ISY) {
+            const int comp = item / (nchunk * lines);
+            line_fft<LOGN, E, (OP == OP_Y_FWD ? -1 : +1)>(v, j, S, g.t.tw);
             if (valid) {
+                float2* out = a.out[comp] + (size_t)line * g.ny * g.nhp + col;
 #pragma unroll
-                for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, w[m]);
+                for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * g.nhp, v[m]);
+            }
+        } else {
+            const int y = line;
+            const size_t es = (size_t)g.ny * g.nhp;
+            const size_t off = (size_t)y * g.nhp + col;
+            const float kx = col < g.nh ? __ldg(g.t.kx + col) : 0.f;
+            const float ky = __ldg(g.t.ky + y);
+            if (l == 0) {                            // operator values of this tile, kept for its loads
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const float kz = __ldg(g.t.kz + j + TL * m);
+                    const float k2 = fmaf(kx, kx, fmaf(ky, ky, kz * kz));
+                    if (OP == OP_Z_ABS) lg[m] = k2 > 0.f ? log2f(k2 * g.inv_kmax2) : -INFINITY;
+                    else kap[m] = sinc_f(g.hk * sqrtf(k2)) * g.scale;
+                }
+            }
+            line_fft<LOGN, E, -1>(v, j, S, g.t.tw);
+            if (OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) {
+                const float2 dx = col < g.nh ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
+                const float2 dy = __ldg(g.t.dfy + y);
+#pragma unroll 1
+                for (int xi = 0; xi < 3; ++xi) {
+                    float2* out = a.out[xi];
+                    if (out == nullptr) continue;   // uniform
+                    float2 w[E];
+#pragma unroll
+                    for (int m = 0; m < E; ++m) {
+                        float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
+                        if (OP == OP_Z_GRAD_BWD) d = make_float2(-d.x, d.y);   // i k e^{-ikd/2}
+                        w[m] = cscale(cmul(v[m], d), kap[m]);
+                    }
+                    line_fft<LOGN, E, +1>(w, j, S, g.t.tw);
+                    if (valid) {
+#pragma unroll
+                        for (int m = 0; m < E; ++m) __stcs(out + off + (size_t)(j + TL * m) * es, w[m]);
+                    }
+                }
+            } else if (OP == OP_Z_DIV) {
+                const int xi = l;
+                const float2 dx = col < g.nh ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
+                const float2 dy = __ldg(g.t.dfy + y);
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
+                    d = make_float2(-d.x, d.y);            // Eq. 4c: i k e^{-ikd/2}
+                    v[m] = cscale(cmul(v[m], d), kap[m]);
+                }
+                line_fft<LOGN, E, +1>(v, j, S, g.t.tw);
+                if (valid) {
+                    float2* out = a.out[xi] + off;
+#pragma unroll
+                    for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
+                }
+            } else {                                   // OP_Z_ABS
+                const int t = a.load_comp[l];
+                const float e = g.abs_e[t], cst = g.abs_c[t] * g.scale;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const float f = lg[m] > -INFINITY ? exp2f(e * lg[m]) * cst : 0.f;   // k^{y-2} / k^{y-1}, 0 at k = 0
+                    v[m] = cscale(v[m], f);
+                }
+                line_fft<LOGN, E, +1>(v, j, S, g.t.tw);
+                if (valid) {
+                    float2* out = a.out[t] + off;
+#pragma unroll
+                    for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
+                }
             }
         }
-    } else if (OP == Z_DIV) {
-        float kap[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) kap[m] = sinc_f(g.hk * sqrtf(k2[m])) * g.scale;
-        const float2 dx = valid ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
-        const float2 dy = __ldg(g.t.dfy + y);
-#pragma unroll 1
-        for (int xi = 0; xi < 3; ++xi) {
-            const float2* __restrict__ in = a.in[xi] + off;
-            float2* __restrict__ out = a.out[xi] + off;
-            float2 v[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m)
-                v[m] = valid ? __ldcs(in + (size_t)(j + TL * m) * es) : make_float2(0.f, 0.f);
-            line_fft<LOGN, E, -1>(v, j, S, g.t.tw);
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
-                d = make_float2(-d.x, d.y);        // Eq. 4c: i k e^{-ikd/2}
-                v[m] = cscale(cmul(v[m], d), kap[m]);
-            }
-            line_fft<LOGN, E, +1>(v, j, S, g.t.tw);
-            if (valid) {
-#pragma unroll
-                for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
-            }
-        }
-    } else {  // Z_ABS
-        float lg[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) lg[m] = k2[m] > 0.f ? log2f(k2[m] * g.inv_kmax2) : 0.f;
-#pragma unroll 1
-        for (int t = 0; t < 2; ++t) {
-            if (a.in[t] == nullptr) continue;      // uniform
-            const float2* __restrict__ in = a.in[t] + off;
-            float2* __restrict__ out = a.out[t] + off;
-            float2 v[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m)
-                v[m] = valid ? __ldcs(in + (size_t)(j + TL * m) * es) : make_float2(0.f, 0.f);
-            line_fft<LOGN, E, -1>(v, j, S, g.t.tw);
-            const float e = g.abs_e[t], cst = g.abs_c[t] * g.scale;
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const float f = k2[m] > 0.f ? exp2f(e * lg[m]) * cst : 0.f;   // k^{y-2} or k^{y-1}, 0 at k = 0
-                v[m] = cscale(v[m], f);
-            }
-            line_fft<LOGN, E, +1>(v, j, S, g.t.tw);
-            if (valid) {
-#pragma unroll
-                for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
-            }
+        __syncthreads();                          // stage s is free for the load of q + 2
+        if (abort_flag) {
+            if (tid == 0 && q + 1 < Q) mbar_wait_bounded(&bar[(q + 1) & 1], ((q + 1) >> 1) & 1, a.flag);
+            return;
         }
     }
 }
 
-template <int LOGN, int DIR>
-static cudaError_t launch_y_t(const YArgs& a, int ncomp, cudaStream_t s) {
-    using Sh = YZShape<LOGN>;
-    auto k = y_pass_kernel<LOGN, DIR>;
-    if (Sh::SMEM > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
-        if (e != cudaSuccess) return e;
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
     }
-    dim3 grid((a.g.nh + Sh::CX - 1) / Sh::CX, a.g.nz, ncomp);
-    k<<<grid, Sh::THREADS, Sh::SMEM, s>>>(a);
-    return cudaGetLastError();
+    return fn;
 }
 
-template <int LOGN, int OP>
-static cudaError_t launch_z_t(const ZArgs& a, cudaStream_t s) {
-    using Sh = YZShape<LOGN>;
-    auto k = z_op_kernel<LOGN, OP>;
-    if (Sh::SMEM > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid((a.g.nh + Sh::CX - 1) / Sh::CX, a.g.ny, 1);
-    k<<<grid, Sh::THREADS, Sh::SMEM, s>>>(a);
-    return cudaGetLastError();
+template <int LOGN, bool ISY>
+static int encode_box(const GridC& g, float2* ptr, CUtensorMap* map) {
+    using Sh = TShape<LOGN, ISY>;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return -1;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nh, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nhp * 8, (cuuint64_t)g.ny * g.nhp * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)Sh::CX, ISY ? (cuuint32_t)Sh::BOX : 1u, ISY ? 1u : (cuuint32_t)Sh::BOX};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, ptr, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -2;
 }
 
 #define KWGB_LOG_CASES(X) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 
-cudaError_t launch_y_pass(const GridC& g, int dir, float2* const* in, float2* const* out,
-                          int ncomp, cudaStream_t s) {
-    YArgs a;
-    a.g = g;
-    for (int i = 0; i < 3; ++i) {
-        a.in[i] = i < ncomp ? in[i] : nullptr;
-        a.out[i] = i < ncomp ? out[i] : nullptr;
-    }
+int make_spec_maps(const GridC& g, float2* ptr, SpecBuf* out) {
+    out->p = ptr;
+    int e = -3;
     switch (g.logny) {
-#define CASE(L) case L: return dir < 0 ? launch_y_t<L, -1>(a, ncomp, s) : launch_y_t<L, +1>(a, ncomp, s);
+#define CASE(L) case L: e = encode_box<L, true>(g, ptr, &out->ymap); break;
         KWGB_LOG_CASES(CASE)
 #undef CASE
     }
-    return cudaErrorInvalidValue;
+    if (e) return e;
+    switch (g.lognz) {
+#define CASE(L) case L: e = encode_box<L, false>(g, ptr, &out->zmap); break;
+        KWGB_LOG_CASES(CASE)
+#undef CASE
+    }
+    return e;
+}
+
+template <int LOGN, int OP>
+static cudaError_t launch_t(const YZK& a, int items, cudaStream_t s) {
+    using Sh = TShape<LOGN, (OP < 2)>;
+    auto k = yz_kernel<LOGN, OP>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Sh::THREADS, Sh::SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    int grid = per_sm * a.g.num_sms;
+    if (grid > items) grid = items;
+    if (grid < 1) return cudaSuccess;
+    k<<<grid, Sh::THREADS, Sh::SMEM, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int OP>
-static cudaError_t launch_z_op_k(const ZArgs& a, cudaStream_t s) {
-    switch (a.g.lognz) {
-#define CASE(L) case L: return launch_z_t<L, OP>(a, s);
+static cudaError_t launch_op(const YZK& a, int logn, int items, cudaStream_t s) {
+    switch (logn) {
+#define CASE(L) case L: return launch_t<L, OP>(a, items, s);
         KWGB_LOG_CASES(CASE)
 #undef CASE
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_z_op(const GridC& g, int kind, float2* const* in, float2* const* out,
-                        cudaStream_t s) {
-    ZArgs a;
+static int chunk_count(int nh, int cx) { return (nh + cx - 1) / cx; }
+
+template <bool ISY>
+static int cx_of(int logn) {
+    switch (logn) {
+#define CASE(L) case L: return TShape<L, ISY>::CX;
+        KWGB_LOG_CASES(CASE)
+#undef CASE
+    }
+    return 16;
+}
+
+cudaError_t launch_y_pass(const GridC& g, int dir, const SpecBuf* const* in, float2* const* out,
+                          int ncomp, int* flag, cudaStream_t s) {
+    YZK a;
+    memset(&a, 0, sizeof(a));
     a.g = g;
-    for (int i = 0; i < 3; ++i) {
-        a.in[i] = in[i];
+    for (int i = 0; i < ncomp; ++i) {
+        a.map[i] = in[i]->ymap;
         a.out[i] = out[i];
     }
+    a.ncomp = ncomp;
+    a.nloads = 1;
+    a.flag = flag;
+    const int items = chunk_count(g.nh, cx_of<true>(g.logny)) * g.nz * ncomp;
+    return dir < 0 ? launch_op<OP_Y_FWD>(a, g.logny, items, s) : launch_op<OP_Y_INV>(a, g.logny, items, s);
+}
+
+cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, float2* const* out, int* flag,
+                        cudaStream_t s) {
+    YZK a;
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.flag = flag;
+    for (int i = 0; i < 3; ++i) a.out[i] = out[i];
+    if (kind == Z_GRAD_FWD || kind == Z_GRAD_BWD) {
+        a.map[0] = in[0]->zmap;
+        a.nloads = 1;
+        a.load_comp[0] = 0;
+    } else if (kind == Z_DIV) {
+        for (int i = 0; i < 3; ++i) {
+            a.map[i] = in[i]->zmap;
+            a.load_comp[i] = i;
+        }
+        a.nloads = 3;
+    } else {
+        int n = 0;
+        for (int t = 0; t < 2; ++t)
+            if (in[t]) {
+                a.map[t] = in[t]->zmap;
+                a.load_comp[n++] = t;
+            }
+        a.nloads = n;
+        if (n == 0) return cudaSuccess;
+    }
+    const int items = chunk_count(g.nh, cx_of<false>(g.lognz)) * g.ny;
     switch (kind) {
-        case Z_GRAD_FWD: return launch_z_op_k<Z_GRAD_FWD>(a, s);
-        case Z_GRAD_BWD: return launch_z_op_k<Z_GRAD_BWD>(a, s);
-        case Z_DIV: return launch_z_op_k<Z_DIV>(a, s);
-        case Z_ABS: return launch_z_op_k<Z_ABS>(a, s);
+        case Z_GRAD_FWD: return launch_op<OP_Z_GRAD_FWD>(a, g.lognz, items, s);
+        case Z_GRAD_BWD: return launch_op<OP_Z_GRAD_BWD>(a, g.lognz, items, s);
+        case Z_DIV: return launch_op<OP_Z_DIV>(a, g.lognz, items, s);
+        case Z_ABS: return launch_op<OP_Z_ABS>(a, g.lognz, items, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -3,6 +3,7 @@
 // host-side launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,8 +33,18 @@ struct GridC {
     float inv_kmax2;          // 1 / max k^2
     float abs_e[2];           // (y-2)/2, (y-1)/2: powers of k^2 / kmax^2 in Eq. 8
     float abs_c[2];           // kmax^(y-2), kmax^(y-1)
+    int num_sms;              // SMs of the device (persistent grids)
     Tables t;
 };
+
+// A spectrum buffer with the TMA tensor maps of its y-pass and z-pass tiles.
+struct SpecBuf {
+    float2* p;
+    CUtensorMap ymap;
+    CUtensorMap zmap;
+};
+// Encode the two tensor maps of a spectrum buffer (0 on success).
+int make_spec_maps(const GridC& g, float2* ptr, SpecBuf* out);
 
 struct Medium {
     const float* c0;          // NULL -> scalar value below
@@ -77,17 +88,18 @@ struct StepC {
 };
 
 // ---- launchers (return the launch error) --------------------------------
-// y pass on ncomp spectra: in[c] -> out[c] (in place allowed); dir -1 forward, +1 inverse
-cudaError_t launch_y_pass(const GridC& g, int dir, float2* const* in, float2* const* out,
-                          int ncomp, cudaStream_t s);
+// y pass on ncomp spectra: in[c] -> out[c] (in place allowed); dir -1 forward, +1 inverse.
+// flag receives bit 2 if a bounded TMA wait runs out.
+cudaError_t launch_y_pass(const GridC& g, int dir, const SpecBuf* const* in, float2* const* out,
+                          int ncomp, int* flag, cudaStream_t s);
 
 enum ZOpKind { Z_GRAD_FWD = 0, Z_GRAD_BWD = 1, Z_DIV = 2, Z_ABS = 3 };
 // z forward FFT -> operator -> z inverse FFT:
 //   Z_GRAD_*: in[0] -> out[xi] (NULL skips a component)
 //   Z_DIV:    in[xi] -> out[xi]  (Eq. 4c operator)
 //   Z_ABS:    in[0] -> out[0] with k^{y-2}, in[1] -> out[1] with k^{y-1} (NULL skips)
-cudaError_t launch_z_op(const GridC& g, int kind, float2* const* in, float2* const* out,
-                        cudaStream_t s);
+cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, float2* const* out,
+                        int* flag, cudaStream_t s);
 
 enum XVelMode { XV_STEP = 0, XV_TAIL = 1, XV_INIT = 2 };
 struct XVelArgs {
