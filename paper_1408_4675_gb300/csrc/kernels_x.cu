@@ -53,10 +53,16 @@ __device__ __forceinline__ void row_c2r(const float2* __restrict__ spec, RowSmem
                                         float2 (&z)[XShape<LOGM>::E]) {
     using Sh = XShape<LOGM>;
     constexpr int M = Sh::M, E = Sh::E, TL = Sh::TL;
+    // all E + 1 loads of the row are issued before the first one is used
+    float2 t[E];
+    float2 nyq = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < E; ++m) t[m] = valid ? __ldcs(spec + j + TL * m) : make_float2(0.f, 0.f);
+    if (valid && j == 0) nyq = __ldcs(spec + M);
     __syncwarp();                                  // smem row free
-    if (valid) {
-        for (int k = j; k <= M; k += TL) S.at(k) = __ldcs(spec + k);
-    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) S.at(j + TL * m) = t[m];
+    if (j == 0) S.at(M) = nyq;
     __syncwarp();
 #pragma unroll
     for (int m = 0; m < E; ++m) {

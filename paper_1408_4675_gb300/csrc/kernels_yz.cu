@@ -63,8 +63,13 @@ __device__ __forceinline__ float sinc_f(float x) {
     return fabsf(x) < 1e-4f ? 1.0f - x * x * (1.0f / 6.0f) : sinf(x) / x;
 }
 
+// a.out[i] for a run-time i without copying the parameter array to local memory
+__device__ __forceinline__ float2* out_ptr(const YZK& a, int i) {
+    return i == 0 ? a.out[0] : (i == 1 ? a.out[1] : a.out[2]);
+}
+
 template <int LOGN, int OP>
-__global__ void __launch_bounds__(TShape<LOGN, (OP < 2)>::THREADS, 1)
+__global__ void __launch_bounds__(TShape<LOGN, (OP < 2)>::THREADS, (OP < 2) ? 1 : 2)
 yz_kernel(const __grid_constant__ YZK a) {
     constexpr bool ISY = OP < 2;
     using Sh = TShape<LOGN, ISY>;
@@ -78,7 +83,10 @@ yz_kernel(const __grid_constant__ YZK a) {
     const int nchunk = (g.nh + CX - 1) / CX;
     const int lines = ISY ? g.nz : g.ny;
     const int items = nchunk * lines * (ISY ? a.ncomp : 1);
-    const int L = ISY ? 1 : a.nloads;
+    // loads per tile: compile-time where the operator fixes it, so that values kept
+    // for the loads of a tile are provably dead at the end of the tile
+    constexpr int LC = (ISY || OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) ? 1 : (OP == OP_Z_DIV ? 3 : 0);
+    const int L = LC ? LC : a.nloads;
     const int my = items > (int)blockIdx.x ? (items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int Q = my * L;
 
@@ -95,8 +103,8 @@ yz_kernel(const __grid_constant__ YZK a) {
         const int l = q % L;
         const int chunk = item % nchunk;
         const int line = (item / nchunk) % lines;
-        const int mi = ISY ? item / (nchunk * lines) : a.load_comp[l];
-        const CUtensorMap* map = &a.map[mi];
+        const int mi = ISY ? item / (nchunk * lines) : (l == 0 ? a.load_comp[0] : (l == 1 ? a.load_comp[1] : a.load_comp[2]));
+        const CUtensorMap* map = mi == 0 ? &a.map[0] : (mi == 1 ? &a.map[1] : &a.map[2]);
         float2* dst = smem + (q & 1) * STAGE;
         uint64_t* b = &bar[q & 1];
         fence_proxy_async_smem();
@@ -134,7 +142,7 @@ yz_kernel(const __grid_constant__ YZK a) {
             const int comp = item / (nchunk * lines);
             line_fft<LOGN, E, (OP == OP_Y_FWD ? -1 : +1)>(v, j, S, g.t.tw);
             if (valid) {
-                float2* out = a.out[comp] + (size_t)line * g.ny * g.nhp + col;
+                float2* out = out_ptr(a, comp) + (size_t)line * g.ny * g.nhp + col;
 #pragma unroll
                 for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * g.nhp, v[m]);
             }
@@ -155,18 +163,21 @@ yz_kernel(const __grid_constant__ YZK a) {
             }
             line_fft<LOGN, E, -1>(v, j, S, g.t.tw);
             if (OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) {
+                // kappa (and the 1/N normalisation) is common to the three outputs
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[m] = cscale(v[m], kap[m]);
                 const float2 dx = col < g.nh ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
                 const float2 dy = __ldg(g.t.dfy + y);
 #pragma unroll 1
                 for (int xi = 0; xi < 3; ++xi) {
-                    float2* out = a.out[xi];
+                    float2* out = out_ptr(a, xi);
                     if (out == nullptr) continue;   // uniform
                     float2 w[E];
 #pragma unroll
                     for (int m = 0; m < E; ++m) {
                         float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
                         if (OP == OP_Z_GRAD_BWD) d = make_float2(-d.x, d.y);   // i k e^{-ikd/2}
-                        w[m] = cscale(cmul(v[m], d), kap[m]);
+                        w[m] = cmul(v[m], d);
                     }
                     line_fft<LOGN, E, +1>(w, j, S, g.t.tw);
                     if (valid) {
@@ -186,12 +197,12 @@ yz_kernel(const __grid_constant__ YZK a) {
                 }
                 line_fft<LOGN, E, +1>(v, j, S, g.t.tw);
                 if (valid) {
-                    float2* out = a.out[xi] + off;
+                    float2* out = out_ptr(a, xi) + off;
 #pragma unroll
                     for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
                 }
             } else {                                   // OP_Z_ABS
-                const int t = a.load_comp[l];
+                const int t = l == 0 ? a.load_comp[0] : a.load_comp[1];
                 const float e = g.abs_e[t], cst = g.abs_c[t] * g.scale;
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
@@ -200,7 +211,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                 }
                 line_fft<LOGN, E, +1>(v, j, S, g.t.tw);
                 if (valid) {
-                    float2* out = a.out[t] + off;
+                    float2* out = out_ptr(a, t) + off;
 #pragma unroll
                     for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
                 }
