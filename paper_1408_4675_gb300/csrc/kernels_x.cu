@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(XTHREADS, 2) x_vel_kernel(const XVelK K) {
     float2 r0[E];                                     // rho0 of this row (x = 2n, 2n+1)
 #pragma unroll
     for (int m = 0; m < E; ++m) r0[m] = rho0 ? ldg2(rho0 + rb + 2 * (j + TL * m)) : make_float2(rho0s, rho0s);
-#pragma unroll 1
+#pragma unroll
     for (int xi = 0; xi < 3; ++xi) {
         // issue this component's field loads before the row transform
         size_t nb;                                    // row base of the +1 neighbour along y / z
@@ -222,11 +222,11 @@ __global__ void __launch_bounds__(XTHREADS, 2) x_vel_kernel(const XVelK K) {
             float2 un;
             if (MODE == XV_INIT) {
                 // u^{-1/2} = +dt / (2 rho0_sg) d/dxi p0
-                un = make_float2(0.5f * g.dt * gr.x / rs.x, 0.5f * g.dt * gr.y / rs.y);
+                un = make_float2(__fdividef(0.5f * g.dt * gr.x, rs.x), __fdividef(0.5f * g.dt * gr.y, rs.y));
             } else {
                 // Eq. 4b with the PML: u <- f (f u - dt grad p / rho0_sg)
-                un = make_float2(f.x * (f.x * uo[m].x - g.dt * gr.x / rs.x),
-                                 f.y * (f.y * uo[m].y - g.dt * gr.y / rs.y));
+                un = make_float2(f.x * (f.x * uo[m].x - __fdividef(g.dt * gr.x, rs.x)),
+                                 f.y * (f.y * uo[m].y - __fdividef(g.dt * gr.y, rs.y)));
             }
             if (valid) {
                 if (MODE == XV_TAIL) st2(K.a.tail[xi] + (size_t)rr * 2 * g.nhp + x, un);
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(XTHREADS, 2) x_dens_kernel(const XDensK K) {
             }
             const int x = __ldg(K.src.pt_x + p);
             const float c = md.c0 ? __ldg(md.c0 + rb + x) : md.c0_s;
-            S.f(x) = acc / c;                          // dt * 2 s / (3 c0 dx)
+            S.f(x) = __fdividef(acc, c);               // dt * 2 s / (3 c0 dx)
         }
         __syncwarp();
         if (p1 > p0) {
@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(XTHREADS, 2) x_dens_kernel(const XDensK K) {
             float nx_ = f.x * (f.x * ro.x - g.dt * r0[m].x * d[m].x);
             float ny_ = f.y * (f.y * ro.y - g.dt * r0[m].y * d[m].y);
             if (md.nonlinear) {
-                nx_ = nx_ / (1.0f + 2.0f * g.dt * d[m].x);
-                ny_ = ny_ / (1.0f + 2.0f * g.dt * d[m].y);
+                nx_ = __fdividef(nx_, 1.0f + 2.0f * g.dt * d[m].x);
+                ny_ = __fdividef(ny_, 1.0f + 2.0f * g.dt * d[m].y);
             }
             const float2 rn = make_float2(nx_ + sv[m].x, ny_ + sv[m].y);
             if (valid) st2(K.a.rho[xi] + rb + x, rn);
@@ -342,8 +342,8 @@ __global__ void __launch_bounds__(XTHREADS, 2) x_dens_kernel(const XDensK K) {
             float2 q = rho;
             if (md.nonlinear) {
                 const float2 ba = med2(md.bona, md.bona_s, i);
-                q.x += 0.5f * ba.x * rho.x * rho.x / r0[m].x;
-                q.y += 0.5f * ba.y * rho.y * rho.y / r0[m].y;
+                q.x += __fdividef(0.5f * ba.x * rho.x * rho.x, r0[m].x);
+                q.y += __fdividef(0.5f * ba.y * rho.y * rho.y, r0[m].y);
             }
             s[m] = make_float2(c.x * c.x * q.x, c.y * c.y * q.y);
         }
@@ -401,8 +401,8 @@ __global__ void __launch_bounds__(XTHREADS, 2) x_eos_kernel(const XEosK K) {
         if (md.nonlinear) {
             const float2 r0 = med2(md.rho0, md.rho0_s, i);
             const float2 ba = med2(md.bona, md.bona_s, i);
-            q.x += 0.5f * ba.x * rho.x * rho.x / r0.x;
-            q.y += 0.5f * ba.y * rho.y * rho.y / r0.y;
+            q.x += __fdividef(0.5f * ba.x * rho.x * rho.x, r0.x);
+            q.y += __fdividef(0.5f * ba.y * rho.y * rho.y, r0.y);
         }
         const float cx2 = c.x * c.x, cy2 = c.y * c.y;
         const float px = exp2f(ym1 * log2f(c.x)), py = exp2f(ym1 * log2f(c.y));   // c0^{y-1}

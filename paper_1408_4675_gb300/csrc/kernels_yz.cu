@@ -58,9 +58,23 @@ struct alignas(64) YZK {
     int* flag;
 };
 
-// sinc(x) = sin(x)/x with sinc(0) = 1 (kappa of Sec. 2.2)
+// sinc(x) = sin(x)/x with sinc(0) = 1 (kappa of Sec. 2.2).  For |x| <= 3 the
+// Taylor series sum_n (-x^2)^n / (2n+1)! up to n = 9 is used (branch-free; the
+// truncation error is below the n = 10 term, 3^20/21! < 7e-11); beyond that
+// sin(x)/x directly.
 __device__ __forceinline__ float sinc_f(float x) {
-    return fabsf(x) < 1e-4f ? 1.0f - x * x * (1.0f / 6.0f) : sinf(x) / x;
+    const float x2 = x * x;
+    if (x2 > 9.0f) return __fdividef(sinf(x), x);
+    float p = -1.0f / 121645100408832000.0f;          // -1/19!
+    p = fmaf(p, x2, 1.0f / 355687428096000.0f);       //  1/17!
+    p = fmaf(p, x2, -1.0f / 1307674368000.0f);        // -1/15!
+    p = fmaf(p, x2, 1.0f / 6227020800.0f);            //  1/13!
+    p = fmaf(p, x2, -1.0f / 39916800.0f);             // -1/11!
+    p = fmaf(p, x2, 1.0f / 362880.0f);                //  1/9!
+    p = fmaf(p, x2, -1.0f / 5040.0f);                 // -1/7!
+    p = fmaf(p, x2, 1.0f / 120.0f);                   //  1/5!
+    p = fmaf(p, x2, -1.0f / 6.0f);                    // -1/3!
+    return fmaf(p, x2, 1.0f);
 }
 
 // a.out[i] for a run-time i without copying the parameter array to local memory
