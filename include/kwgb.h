@@ -180,6 +180,32 @@ int kwgb_read_field(kwgb_sim* sim, int field, float* host_out, int64_t n);
 int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float* out0,
                         float* out1, float* out2, void* cuda_stream);
 
+/* Allocation-free form of the staggered gradient that kwgb_apply_operator
+ * computes for KWGB_OP_GRAD_FWD / KWGB_OP_GRAD_BWD (the paper has no
+ * counterpart: it is an interface for callers that cannot allocate device
+ * memory, such as code whose device memory is owned entirely by another
+ * allocator or a fixed arena, and code that must not allocate after start-up,
+ * where cudaMalloc may synchronise the device or fail).
+ *   desc      grid: nx, ny, nz powers of two in [8, 64]; dx, dy, dz, dt, c_ref
+ *             (pml_*, flags and alpha_power are ignored); no simulation needed
+ *   op        KWGB_OP_GRAD_FWD (Eq. 4a) or KWGB_OP_GRAD_BWD (Eq. 4c)
+ *   in        device field, nx*ny*nz floats, [nz][ny][nx]
+ *   out_x/y/z device outputs, nx*ny*nz floats each (not aliasing in)
+ *   err       optional buffer (errlen bytes) that receives a message on failure
+ * Asynchronous on cuda_stream.  It allocates nothing and calls no cudaMalloc
+ * or cudaFree: its scratch (three spectra and small tables) is one file-scope
+ * device array of about 4.7 MB that every GPU loading the library holds until
+ * the process exits.  Larger grids are rejected with KWGB_ERR_UNSUPPORTED.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make this first call before any stream capture.
+ * All calls share the array and it keeps the previous call's contents (each
+ * call clears its status word and overwrites everything else it reads), so
+ * calls that overlap on the GPU, e.g. from two streams, race and must be
+ * serialised by the caller.  Errors: ARG, UNSUPPORTED, CUDA. */
+int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const float* in, float* out_x,
+                         float* out_y, float* out_z, void* cuda_stream, char* err,
+                         size_t errlen);
+
 /* Number of steps taken so far. */
 int64_t kwgb_steps_done(const kwgb_sim* sim);
 

@@ -1,0 +1,183 @@
+// Allocation-free staggered spectral gradient (kwgb_gradient_static).
+//
+// Some callers cannot allocate device memory when they need this operation:
+// code whose device memory is owned entirely by another allocator (a
+// framework's memory pool, or a fixed arena sized once at start-up), and
+// code paths that must not allocate after initialisation, because cudaMalloc
+// can synchronise the device and can fail once memory has been committed
+// elsewhere.  This entry point therefore takes its scratch space from one
+// file-scope __device__ array instead of allocating.  The array is created
+// when the library is loaded and every GPU that loads the library holds it
+// until the process exits: about 4.7 MB, enough for grids up to 64 x 64 x 64.
+//
+// The operation is the same chain kwgb_apply_operator runs for
+// KWGB_OP_GRAD_FWD / KWGB_OP_GRAD_BWD (x R2C, y FFT, z FFT + operator + z
+// inverse, y inverse, x C2R) through the same kernels; only the scratch
+// spectra and the small tables live in the static array.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/kwgb.h"
+#include "kwgb_internal.h"
+
+using namespace kwgb;
+
+namespace {
+
+constexpr int kMaxN = 64;                                          // largest nx, ny, nz
+constexpr int kMaxNhp = ((kMaxN / 2 + 1) + 15) / 16 * 16;          // padded spectrum pitch
+constexpr size_t kSpec = (size_t)kMaxNhp * kMaxN * kMaxN;          // complex per spectrum
+// layout of the scratch array, in float2 units (every block 256-byte aligned)
+constexpr size_t kOffSpec = 0;                                     // 3 spectra
+constexpr size_t kOffTw = 3 * kSpec;                               // 1024 twiddles
+constexpr size_t kOffK = kOffTw + 1024;                            // kx, ky, kz (float)
+constexpr size_t kOffDf = kOffK + 128;                             // dfx, dfy, dfz (kx.. take 256 floats)
+constexpr size_t kOffFlag = kOffDf + 256;                          // device status word
+constexpr size_t kTotal = kOffFlag + 32;
+constexpr int kMaxDevices = 64;
+constexpr double kPi = 3.14159265358979323846;
+
+// Copy msg into the caller's optional error buffer and return code.
+int report(char* buf, size_t len, int code, const char* msg) {
+    if (buf && len > 0) {
+        std::strncpy(buf, msg, len - 1);
+        buf[len - 1] = 0;
+    }
+    return code;
+}
+
+std::mutex g_setup_mu;
+float2* g_base[kMaxDevices];     // device address of the scratch array, per device
+int g_sms[kMaxDevices];
+
+}  // namespace
+
+// The scratch: three spectra plus the tables of the chain.  Host code must not
+// pass this symbol to a kernel (on the host it only stands in for the device
+// array); the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) float2 g_static_scratch[kTotal];
+
+// Once per device, with that device current: look up the scratch array's
+// device address and the SM count.
+static int static_setup(int dev, float2** base, int* sms, char* err, size_t errlen) {
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (g_base[dev] == nullptr) {
+        float2* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_static_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return report(err, errlen, KWGB_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+        }
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return report(err, errlen, KWGB_ERR_CUDA, "cudaDeviceGetAttribute failed");
+        g_sms[dev] = n;
+        g_base[dev] = p;
+    }
+    *base = g_base[dev];
+    *sms = g_sms[dev];
+    return KWGB_OK;
+}
+
+static double wavenumber_static(int j, int n, double d) {
+    const int m = j < n / 2 ? j : j - n;                  // Eq. 5, even n
+    return (double)m * 2.0 * kPi / (d * (double)n);
+}
+
+static int ilog2_static(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+extern "C" int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const float* in,
+                                    float* out_x, float* out_y, float* out_z, void* cuda_stream,
+                                    char* err, size_t errlen) {
+    report(err, errlen, KWGB_OK, "");
+    if (!desc || !in || !out_x || !out_y || !out_z) return report(err, errlen, KWGB_ERR_ARG, "null argument");
+    if (op != KWGB_OP_GRAD_FWD && op != KWGB_OP_GRAD_BWD)
+        return report(err, errlen, KWGB_ERR_ARG, "op must be KWGB_OP_GRAD_FWD or KWGB_OP_GRAD_BWD");
+    const int64_t n[3] = {desc->nx, desc->ny, desc->nz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 8 || n[a] > kMaxN || (n[a] & (n[a] - 1)))
+            return report(err, errlen, KWGB_ERR_UNSUPPORTED,
+                               "kwgb_gradient_static serves nx, ny, nz powers of two in [8, 64] only");
+    }
+    const double dd[3] = {desc->dx, desc->dy, desc->dz};
+    for (int a = 0; a < 3; ++a)
+        if (!(dd[a] > 0) || !std::isfinite(dd[a])) return report(err, errlen, KWGB_ERR_ARG, "spacing must be positive");
+    if (!(desc->dt > 0) || !(desc->c_ref > 0)) return report(err, errlen, KWGB_ERR_ARG, "dt and c_ref must be positive");
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return report(err, errlen, KWGB_ERR_CUDA, "no usable current device");
+    float2* base = nullptr;
+    int sms = 0;
+    if (int e = static_setup(dev, &base, &sms, err, errlen)) return e;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    GridC g;
+    std::memset(&g, 0, sizeof(g));
+    g.nx = (int)n[0]; g.ny = (int)n[1]; g.nz = (int)n[2];
+    g.nh = g.nx / 2 + 1;
+    g.nhp = (g.nh + 15) / 16 * 16;
+    g.lognx = ilog2_static(g.nx); g.logny = ilog2_static(g.ny); g.lognz = ilog2_static(g.nz);
+    g.dt = (float)desc->dt;
+    g.scale = (float)(1.0 / ((double)g.nx * g.ny * g.nz));
+    g.hk = (float)(desc->c_ref * desc->dt / 2.0);
+    g.num_sms = sms;
+
+    // tables, built here in float64 and copied into the scratch (fixed-size host arrays)
+    float2 tw[1024];
+    for (int t = 0; t < 1024; ++t) {
+        const double a = 2.0 * kPi * t / 1024.0;
+        tw[t] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    float kt[256];
+    float2 df[256];
+    const int klen[3] = {g.nh, g.ny, g.nz};
+    const int koff[3] = {0, kMaxN / 2 + 1, kMaxN / 2 + 1 + kMaxN};
+    const int doff[3] = {0, 64, 128};
+    for (int a = 0; a < 3; ++a)
+        for (int j = 0; j < klen[a]; ++j) {
+            const double k = wavenumber_static(j, (int)n[a], dd[a]);
+            kt[koff[a] + j] = (float)k;
+            df[doff[a] + j] = make_float2((float)(-k * std::sin(k * dd[a] / 2.0)), (float)(k * std::cos(k * dd[a] / 2.0)));
+        }
+    float* kbase = reinterpret_cast<float*>(base + kOffK);
+    if (cudaMemcpyAsync(base + kOffTw, tw, sizeof(tw), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(kbase, kt, sizeof(kt), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(base + kOffDf, df, sizeof(df), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(base + kOffFlag, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return report(err, errlen, KWGB_ERR_CUDA, "copying the tables into the static scratch failed");
+    }
+    g.t.tw = base + kOffTw;
+    g.t.kx = kbase + koff[0];
+    g.t.ky = kbase + koff[1];
+    g.t.kz = kbase + koff[2];
+    g.t.dfx = base + kOffDf + doff[0];
+    g.t.dfy = base + kOffDf + doff[1];
+    g.t.dfz = base + kOffDf + doff[2];
+    int* flag = reinterpret_cast<int*>(base + kOffFlag);
+
+    // the three scratch spectra, with the tensor maps of their y and z tiles
+    SpecBuf sb[3];
+    for (int i = 0; i < 3; ++i)
+        if (make_spec_maps(g, base + kOffSpec + i * kSpec, &sb[i]) != 0)
+            return report(err, errlen, KWGB_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    float2* sp[3] = {sb[0].p, sb[1].p, sb[2].p};
+    const SpecBuf* in0[3] = {&sb[0], nullptr, nullptr};
+    const SpecBuf* all[3] = {&sb[0], &sb[1], &sb[2]};
+    float* outs[3] = {out_x, out_y, out_z};
+    cudaError_t e = launch_x_r2c(g, in, g.nx, sp[0], s);
+    if (e == cudaSuccess) e = launch_y_pass(g, -1, in0, sp, 1, flag, s);
+    if (e == cudaSuccess) e = launch_z_op(g, op == KWGB_OP_GRAD_FWD ? Z_GRAD_FWD : Z_GRAD_BWD, in0, sp, flag, s);
+    if (e == cudaSuccess) e = launch_y_pass(g, +1, all, sp, 3, flag, s);
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = launch_x_c2r(g, sp[a], outs[a], g.nx, s);
+    if (e != cudaSuccess) return report(err, errlen, KWGB_ERR_CUDA, cudaGetErrorString(e));
+    return KWGB_OK;
+}
