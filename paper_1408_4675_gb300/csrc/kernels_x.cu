@@ -75,6 +75,66 @@ __device__ __forceinline__ void row_c2r(const float2* __restrict__ spec, RowSmem
     line_fft<LOGM, E, +1>(z, j, S, tw);
 }
 
+// ---- asynchronous row staging (per-warp cp.async double buffer) ----------
+// A warp's rows of one spectrum are copied into shared memory one item ahead
+// of their use, so the global-memory latency of the row load overlaps the
+// transform of the previous item.  Rows are copied as M + 2 complex values
+// (a multiple of 16 bytes; the extra value lies in the row padding).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <int LOGM>
+struct XStage {
+    static constexpr int M = 1 << LOGM;
+    static constexpr int SROW = M + 2;                   // staged complex values per row
+    static constexpr int TL = XShape<LOGM>::TL;
+    static constexpr int RPW = 32 / TL;                  // rows per warp
+    static constexpr int WARP = 2 * RPW * SROW;          // complex per warp (two stages)
+};
+
+// Issue the copies of rows first_row .. first_row + RPW - 1 of `spec` into
+// stage buffer `dst` (RPW * SROW complex).  All 32 lanes take part.
+template <int LOGM>
+__device__ __forceinline__ void stage_rows(float2* dst, const float2* __restrict__ spec, int first_row,
+                                           int nrows, int nhp, int lane) {
+    using St = XStage<LOGM>;
+    constexpr int CH = St::SROW / 2;                     // 16-byte chunks per row
+#pragma unroll
+    for (int t = 0; t < (St::RPW * CH + 31) / 32; ++t) {
+        const int c = lane + 32 * t;
+        if (c < St::RPW * CH) {
+            const int r = c / CH, q = c % CH;
+            if (first_row + r < nrows)
+                cp_async16(dst + r * St::SROW + 2 * q, spec + (size_t)(first_row + r) * nhp + 2 * q);
+        }
+    }
+}
+
+// C2R of one row whose half spectrum X[0..M] is already in shared memory
+// (srow, unpadded): same result as row_c2r.
+template <int LOGM>
+__device__ __forceinline__ void row_c2r_staged(const float2* srow, RowSmem& S, int j,
+                                               const float2* __restrict__ tw,
+                                               float2 (&z)[XShape<LOGM>::E]) {
+    using Sh = XShape<LOGM>;
+    constexpr int M = Sh::M, E = Sh::E, TL = Sh::TL;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int k = j + TL * m;
+        const float2 xk = srow[k], xm = cconj(srow[M - k]);
+        const float2 a = cadd(xk, xm);
+        const float2 b = cmul(csub(xk, xm), twiddle1024<+1>(tw, k * (512 / M)));   // exp(+2 pi i k / nx)
+        z[m] = make_float2(a.x - b.y, a.y + b.x);                                // a + i b
+    }
+    __syncwarp();                                    // previous users of the work row are done
+    line_fft<LOGM, E, +1>(z, j, S, tw);
+}
+
 // Unnormalised R2C of one row: z[m] = (x[2n], x[2n+1]) -> spec[0..M].
 template <int LOGM>
 __device__ __forceinline__ void row_r2c(float2 (&z)[XShape<LOGM>::E], RowSmem& S, int j,
@@ -166,6 +226,21 @@ __device__ __forceinline__ void finish_pressure(float2 (&p)[XShape<LOGM>::E], co
 }
 
 // ---------------------------------------------------------------- x_vel
+// p[i] for a run-time i without copying the parameter array to local memory
+__device__ __forceinline__ const float2* pick3(const float2* const (&p)[3], int i) {
+    return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);
+}
+__device__ __forceinline__ float* pick3f(float* const (&p)[3], int i) {
+    return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);
+}
+__device__ __forceinline__ float2* pick3w(float2* const (&p)[3], int i) {
+    return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);
+}
+
+// The fused x kernels are persistent: warp w of the grid handles row groups
+// w, w + W, w + 2W, ... (a group is the 32/TL rows one warp transforms at
+// once), and walks the components of each group as a sequence of items; the
+// spectrum rows of item i+1 are staged while item i is processed.
 struct XVelK {
     GridC g;
     Medium md;
@@ -248,114 +323,146 @@ struct XDensK {
     XDensArgs a;
 };
 
+
 template <int LOGM, bool FUSED_EOS>
 __global__ void __launch_bounds__(XTHREADS, 2) x_dens_kernel(const XDensK K) {
     using Sh = XShape<LOGM>;
-    constexpr int E = Sh::E, TL = Sh::TL;
-    extern __shared__ float2 smem[];
+    using St = XStage<LOGM>;
+    constexpr int E = Sh::E, TL = Sh::TL, RPW = St::RPW, WPB = XTHREADS / 32;
+    extern __shared__ __align__(16) float2 smem[];
     const GridC& g = K.g;
     const Medium& md = K.md;
-    const int r = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = lane / TL, j = lane % TL;
+    RowSmem S{smem + (warp * RPW + r) * Sh::PITCH};
+    float2* stage = smem + Sh::RPB * Sh::PITCH + warp * St::WARP;
     const int nrows = g.ny * g.nz;
-    const int row = blockIdx.x * Sh::RPB + r;
-    const bool valid = row < nrows;
-    const int rr = valid ? row : 0;
-    const int y = rr % g.ny, z = rr / g.ny;
-    RowSmem S{smem + r * Sh::PITCH};
-    const size_t rb = (size_t)rr * g.nx;
+    const int ngroups = (nrows + RPW - 1) / RPW;
+    const int gw = blockIdx.x * WPB + warp, nw = gridDim.x * WPB;
+    const int mygroups = gw < ngroups ? (ngroups - 1 - gw) / nw + 1 : 0;
 
-    // additive mass source of this row (dt M_xi, identical for every xi)
-    float2 sv[E];
+    if (mygroups > 0) stage_rows<LOGM>(stage, K.a.D[0], gw * RPW, nrows, g.nhp, lane);
+    cp_async_commit();
+    for (int gi = 0; gi < mygroups; ++gi) {
+        const int grp = gw + gi * nw;
+        const int row = grp * RPW + r;
+        const bool valid = row < nrows;
+        const int rr = valid ? row : 0;
+        const int y = rr % g.ny, z = rr / g.ny;
+        const size_t rb = (size_t)rr * g.nx;
+
+        float2 s[E], rt[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) sv[m] = make_float2(0.f, 0.f);
-    if (K.src.row_ptr) {                               // uniform over the launch
-        const int p0 = valid ? __ldg(K.src.row_ptr + rr) : 0;
-        const int p1 = valid ? __ldg(K.src.row_ptr + rr + 1) : 0;
-        const int64_t n = *K.st.step;
-        __syncwarp();
-        if (p1 > p0) {
-            for (int x = j; x < g.nx; x += TL) S.f(x) = 0.f;
+        for (int m = 0; m < E; ++m) {
+            s[m] = make_float2(0.f, 0.f);
+            rt[m] = make_float2(0.f, 0.f);
         }
-        __syncwarp();
-        for (int p = p0 + j; p < p1; p += TL) {
-            const int c0 = __ldg(K.src.pt_c + p), c1 = __ldg(K.src.pt_c + p + 1);
-            float acc = 0.f;
-            for (int c = c0; c < c1; ++c) {
-                if (n < __ldg(K.src.c_nt + c))
-                    acc += __ldg(K.src.signal + __ldg(K.src.c_off + c) + n) * __ldg(K.src.c_scale + c);
+        const float fy = __ldg(g.t.pml[1] + y), fz = __ldg(g.t.pml[2] + z);
+#pragma unroll 1
+        for (int xi = 0; xi < 3; ++xi) {
+            const int it = 3 * gi + xi;
+            __syncwarp();
+            if (xi < 2) stage_rows<LOGM>(stage + ((it + 1) & 1) * RPW * St::SROW, pick3(K.a.D, xi + 1), grp * RPW,
+                                         nrows, g.nhp, lane);
+            else if (gi + 1 < mygroups)
+                stage_rows<LOGM>(stage + ((it + 1) & 1) * RPW * St::SROW, K.a.D[0], (grp + nw) * RPW, nrows,
+                                 g.nhp, lane);
+            cp_async_commit();
+            float* rho_xi = pick3f(K.a.rho, xi);
+            float2 ro_[E], r0[E];                     // issued before the row transform (rho0: L1/L2 hits)
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                ro_[m] = valid ? ld2(rho_xi + rb + 2 * (j + TL * m)) : make_float2(0.f, 0.f);
+                r0[m] = med2(md.rho0, md.rho0_s, rb + 2 * (j + TL * m));
             }
-            const int x = __ldg(K.src.pt_x + p);
-            const float c = md.c0 ? __ldg(md.c0 + rb + x) : md.c0_s;
-            S.f(x) = __fdividef(acc, c);               // dt * 2 s / (3 c0 dx)
-        }
-        __syncwarp();
-        if (p1 > p0) {
+            cp_async_wait1();
+            __syncwarp();
+            float2 d[E];
+            row_c2r_staged<LOGM>(stage + (it & 1) * RPW * St::SROW + r * St::SROW, S, j, g.t.tw, d);
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int x = 2 * (j + TL * m);
-                sv[m] = make_float2(S.f(x), S.f(x + 1));
+                const float2 ro = ro_[m];
+                const float2 f = xi == 0 ? ldg2(g.t.pml[0] + x) : (xi == 1 ? make_float2(fy, fy) : make_float2(fz, fz));
+                // Eq. 4d with the PML: rho_xi <- f (f rho_xi - dt rho0 d) / (1 + 2 dt d)
+                float nx_ = f.x * (f.x * ro.x - g.dt * r0[m].x * d[m].x);
+                float ny_ = f.y * (f.y * ro.y - g.dt * r0[m].y * d[m].y);
+                if (md.nonlinear) {
+                    nx_ = __fdividef(nx_, 1.0f + 2.0f * g.dt * d[m].x);
+                    ny_ = __fdividef(ny_, 1.0f + 2.0f * g.dt * d[m].y);
+                }
+                const float2 rn = make_float2(nx_, ny_);
+                if (valid) st2(rho_xi + rb + x, rn);
+                rt[m] = cadd(rt[m], rn);
+                s[m] = make_float2(fmaf(r0[m].x, d[m].x, s[m].x), fmaf(r0[m].y, d[m].y, s[m].y));
             }
         }
-    }
-
-    float2 r0[E], s[E], rt[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-        r0[m] = med2(md.rho0, md.rho0_s, rb + 2 * (j + TL * m));
-        s[m] = make_float2(0.f, 0.f);
-        rt[m] = make_float2(0.f, 0.f);
-    }
-    const float fy = __ldg(g.t.pml[1] + y), fz = __ldg(g.t.pml[2] + z);
-#pragma unroll 1
-    for (int xi = 0; xi < 3; ++xi) {
-        float2 ro_[E];                                // issued before the row transform
-#pragma unroll
-        for (int m = 0; m < E; ++m)
-            ro_[m] = valid ? ld2(K.a.rho[xi] + rb + 2 * (j + TL * m)) : make_float2(0.f, 0.f);
-        float2 d[E];
-        row_c2r<LOGM>(K.a.D[xi] + (size_t)rr * g.nhp, S, j, valid, g.t.tw, d);
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int x = 2 * (j + TL * m);
-            const float2 ro = ro_[m];
-            const float2 f = xi == 0 ? ldg2(g.t.pml[0] + x) : (xi == 1 ? make_float2(fy, fy) : make_float2(fz, fz));
-            // Eq. 4d with the PML: rho_xi <- f (f rho_xi - dt rho0 d) / (1 + 2 dt d)
-            float nx_ = f.x * (f.x * ro.x - g.dt * r0[m].x * d[m].x);
-            float ny_ = f.y * (f.y * ro.y - g.dt * r0[m].y * d[m].y);
-            if (md.nonlinear) {
-                nx_ = __fdividef(nx_, 1.0f + 2.0f * g.dt * d[m].x);
-                ny_ = __fdividef(ny_, 1.0f + 2.0f * g.dt * d[m].y);
+        // additive mass source (dt M_xi, identical for every xi), applied after the
+        // component loop: rho += 3 dt M, and rho_xi += dt M at the (few) source points
+        if (K.src.row_ptr) {                           // uniform over the launch
+            const int p0 = valid ? __ldg(K.src.row_ptr + rr) : 0;
+            const int p1 = valid ? __ldg(K.src.row_ptr + rr + 1) : 0;
+            const int64_t n = *K.st.step;
+            __syncwarp();
+            if (p1 > p0) {
+                for (int x = j; x < g.nx; x += TL) S.f(x) = 0.f;
             }
-            const float2 rn = make_float2(nx_ + sv[m].x, ny_ + sv[m].y);
-            if (valid) st2(K.a.rho[xi] + rb + x, rn);
-            rt[m] = cadd(rt[m], rn);
-            s[m] = make_float2(fmaf(r0[m].x, d[m].x, s[m].x), fmaf(r0[m].y, d[m].y, s[m].y));
-        }
-    }
-    if (FUSED_EOS) {
-        // Eq. 6 without absorption: p = c0^2 (rho + B/2A rho^2 / rho0)
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const size_t i = rb + 2 * (j + TL * m);
-            const float2 c = med2(md.c0, md.c0_s, i);
-            float2 rho = rt[m];
-            float2 q = rho;
-            if (md.nonlinear) {
-                const float2 ba = med2(md.bona, md.bona_s, i);
-                q.x += __fdividef(0.5f * ba.x * rho.x * rho.x, r0[m].x);
-                q.y += __fdividef(0.5f * ba.y * rho.y * rho.y, r0[m].y);
+            __syncwarp();
+            for (int p = p0 + j; p < p1; p += TL) {
+                const int c0 = __ldg(K.src.pt_c + p), c1 = __ldg(K.src.pt_c + p + 1);
+                float acc = 0.f;
+                for (int c = c0; c < c1; ++c) {
+                    if (n < __ldg(K.src.c_nt + c))
+                        acc += __ldg(K.src.signal + __ldg(K.src.c_off + c) + n) * __ldg(K.src.c_scale + c);
+                }
+                const int x = __ldg(K.src.pt_x + p);
+                const float c = md.c0 ? __ldg(md.c0 + rb + x) : md.c0_s;
+                S.f(x) = __fdividef(acc, c);           // dt * 2 s / (3 c0 dx)
             }
-            s[m] = make_float2(c.x * c.x * q.x, c.y * c.y * q.y);
-        }
-        finish_pressure<LOGM>(s, g, K.sens, K.st, S, j, valid, rr, K.a.P);
-    } else {
-        if (valid) {
+            __syncwarp();
+            if (p1 > p0) {
 #pragma unroll
-            for (int m = 0; m < E; ++m)
-                st2(K.a.rho_tot + (size_t)rr * 2 * g.nhp + 2 * (j + TL * m), rt[m]);
+                for (int m = 0; m < E; ++m) {
+                    const int x = 2 * (j + TL * m);
+                    const float2 sv = make_float2(S.f(x), S.f(x + 1));
+                    if (sv.x != 0.f || sv.y != 0.f) {
+#pragma unroll
+                        for (int xi = 0; xi < 3; ++xi) {
+                            float* q = pick3f(K.a.rho, xi) + rb + x;
+                            float2 o = *reinterpret_cast<float2*>(q);
+                            *reinterpret_cast<float2*>(q) = make_float2(o.x + sv.x, o.y + sv.y);
+                        }
+                        rt[m] = make_float2(rt[m].x + 3.0f * sv.x, rt[m].y + 3.0f * sv.y);
+                    }
+                }
+            }
         }
-        row_r2c<LOGM>(s, S, j, valid, g.t.tw, K.a.S + (size_t)rr * g.nhp);
-        row_r2c<LOGM>(rt, S, j, valid, g.t.tw, K.a.R + (size_t)rr * g.nhp);
+        if (FUSED_EOS) {
+            // Eq. 6 without absorption: p = c0^2 (rho + B/2A rho^2 / rho0)
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const size_t i = rb + 2 * (j + TL * m);
+                const float2 c = med2(md.c0, md.c0_s, i);
+                float2 rho = rt[m];
+                float2 q = rho;
+                if (md.nonlinear) {
+                    const float2 ba = med2(md.bona, md.bona_s, i);
+                    const float2 r0 = med2(md.rho0, md.rho0_s, i);
+                    q.x += __fdividef(0.5f * ba.x * rho.x * rho.x, r0.x);
+                    q.y += __fdividef(0.5f * ba.y * rho.y * rho.y, r0.y);
+                }
+                s[m] = make_float2(c.x * c.x * q.x, c.y * c.y * q.y);
+            }
+            finish_pressure<LOGM>(s, g, K.sens, K.st, S, j, valid, rr, K.a.P);
+        } else {
+            if (valid) {
+#pragma unroll
+                for (int m = 0; m < E; ++m)
+                    st2(K.a.rho_tot + (size_t)rr * 2 * g.nhp + 2 * (j + TL * m), rt[m]);
+            }
+            row_r2c<LOGM>(s, S, j, valid, g.t.tw, K.a.S + (size_t)rr * g.nhp);
+            row_r2c<LOGM>(rt, S, j, valid, g.t.tw, K.a.R + (size_t)rr * g.nhp);
+        }
     }
 }
 
@@ -481,6 +588,27 @@ static cudaError_t launch_rows(Kern k, int rpb, int smem_bytes, const GridC& g, 
     return cudaGetLastError();
 }
 
+// Persistent launch of a pipelined row kernel: one CTA per resident slot.
+template <int LOGM, class Kern, class Args>
+static cudaError_t launch_persistent(Kern k, const GridC& g, const Args& args, cudaStream_t s) {
+    using Sh = XShape<LOGM>;
+    using St = XStage<LOGM>;
+    const int smem_bytes = (Sh::RPB * Sh::PITCH + (XTHREADS / 32) * St::WARP) * (int)sizeof(float2);
+    int per_sm = 0;
+    if (smem_bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, XTHREADS, smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int ngroups = (g.ny * g.nz + St::RPW - 1) / St::RPW;
+    int blocks = (ngroups + XTHREADS / 32 - 1) / (XTHREADS / 32);
+    if (blocks > per_sm * g.num_sms) blocks = per_sm * g.num_sms;
+    k<<<blocks, XTHREADS, smem_bytes, s>>>(args);
+    return cudaGetLastError();
+}
+
 #define KWGB_LOGM_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9)
 
 cudaError_t launch_x_vel(const GridC& g, const Medium& m, int mode, const XVelArgs& a,
@@ -506,8 +634,8 @@ cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src,
     switch (g.lognx - 1) {
 #define CASE(L)                                                                                   \
     case L:                                                                                       \
-        if (fused) return launch_rows(x_dens_kernel<L, true>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s); \
-        return launch_rows(x_dens_kernel<L, false>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s);
+        if (fused) return launch_persistent<L>(x_dens_kernel<L, true>, g, K, s); \
+        return launch_persistent<L>(x_dens_kernel<L, false>, g, K, s);
         KWGB_LOGM_CASES(CASE)
 #undef CASE
     }
