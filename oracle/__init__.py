@@ -30,3 +30,4 @@ from .kspace import (  # noqa: F401
     NONLINEAR, ABSORBING, P_MAX, P_RMS, I_AVG, ADDITIVE_MASS,
     OP_GRAD_FWD, OP_DIV_BWD, OP_ABS_TAU, OP_ABS_ETA,
 )
+from . import adjoint  # noqa: F401,E402
