@@ -58,6 +58,9 @@ extern "C" {
 /* ---- source modes ------------------------------------------------------- */
 #define KWGB_ADDITIVE_MASS 0  /* mass source M of Eq. 4d, see kwgb_add_source  */
 
+/* ---- objectives of kwgb_adjoint ----------------------------------------- */
+#define KWGB_OBJ_MEAN_ABS_P 0  /* J = 1/(n_obj Nt) sum_{n=1..Nt} sum_i |p^n(idx_i)| */
+
 /* ---- kwgb_set_medium scalar_mask bits ----------------------------------- */
 #define KWGB_SCALAR_C0      1u
 #define KWGB_SCALAR_RHO0    2u
@@ -205,6 +208,29 @@ int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float* out0,
 int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const float* in, float* out_x,
                          float* out_y, float* out_z, void* cuda_stream, char* err,
                          size_t errlen);
+
+/* Gradient of an objective of the pressure with respect to every source
+ * signal sample, by a hand-written adjoint (reverse-mode) of the time step
+ * (Eqs. 4a-4d and 6 run backwards: the transpose of the Eq. 4a operator is
+ * minus the Eq. 4c operator and vice versa; Eq. 4d and Eq. 6 by their
+ * pointwise derivatives).  The paper has no adjoint; this is the
+ * differentiation form built on its step.
+ *   obj_idx    n_obj unique linear indices (host) of the objective region
+ *   objective  KWGB_OBJ_MEAN_ABS_P (d|p|/dp taken as sign(p))
+ *   n_steps    steps of the run (the simulation must not have stepped yet)
+ *   checkpoint_every  K: the forward keeps the state every K steps; the
+ *              reverse pass recomputes each K-step segment from its
+ *              checkpoint (device memory ~ (n_steps/K) * 7 fields + 6 K fields)
+ *   J_out      objective value (host)
+ *   grad_out   host, grad_len doubles: for every source in add order, its
+ *              n_signals rows of n_t values dJ/dsignal[row][n]
+ * On return the simulation holds the forward end state (n_steps taken) and
+ * its sensors hold the forward run's outputs.  Synchronises.
+ * Errors: ARG, STATE (already stepped), UNSUPPORTED (absorbing medium),
+ * OOM, CUDA, NONFINITE. */
+int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
+                 int64_t n_steps, int64_t checkpoint_every, double* J_out, double* grad_out,
+                 int64_t grad_len, void* cuda_stream);
 
 /* Number of steps taken so far. */
 int64_t kwgb_steps_done(const kwgb_sim* sim);

@@ -91,6 +91,7 @@ struct kwgb_sim {
     float* ubuf = nullptr;
     cudaStream_t last_stream = nullptr;
     int64_t launches = 0;       // kernels launched so far
+    bool adjoint_done = false;
     // per-launch event timing (kwgb_step_profiled)
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -845,6 +846,223 @@ extern "C" int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float
         return KWGB_OK;
     }
     return fail(sim, KWGB_ERR_ARG, "unknown operator");
+}
+
+
+// ------------------------------------------------------------------ adjoint
+// real field r -> spectra (T1, T2, T3) -> y fwd -> z operator -> y inv -> real field
+static int adj_chain(kwgb_sim* sim, float* const in[3], float* const out[3], int kind, cudaStream_t s) {
+    const GridC& g = sim->g;
+    float2* sp[3] = {sim->T1, sim->T2, sim->T3};
+    for (int a = 0; a < 3; ++a) LK(launch_x_r2c(g, in[a], g.nx, sp[a], s));
+    LK(ypass(sim, -1, sp, sp, 3, s));
+    LK(zop(sim, kind, sp, sp, s));
+    LK(ypass(sim, +1, sp, sp, 3, s));
+    for (int a = 0; a < 3; ++a) LK(launch_x_c2r(g, sp[a], out[a], g.nx, s));
+    return KWGB_OK;
+}
+
+static int copy_dev(kwgb_sim* sim, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+    return KWGB_OK;
+}
+
+extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
+                            int64_t n_steps, int64_t checkpoint_every, double* J_out, double* grad_out,
+                            int64_t grad_len, void* cuda_stream) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
+    if (sim->steps != 0 || sim->frozen || sim->adjoint_done)
+        return fail(sim, KWGB_ERR_STATE, "kwgb_adjoint needs a simulation that has not stepped");
+    if (sim->md.absorbing) return fail(sim, KWGB_ERR_UNSUPPORTED, "the adjoint serves lossless media");
+    if (objective != KWGB_OBJ_MEAN_ABS_P) return fail(sim, KWGB_ERR_ARG, "unknown objective");
+    if (!obj_idx || n_obj <= 0 || n_steps <= 0 || checkpoint_every <= 0 || !J_out)
+        return fail(sim, KWGB_ERR_ARG, "bad objective, step count or checkpoint interval");
+    {
+        std::vector<int64_t> u(obj_idx, obj_idx + n_obj);
+        std::sort(u.begin(), u.end());
+        for (size_t i = 0; i < u.size(); ++i)
+            if (u[i] < 0 || u[i] >= sim->N || (i && u[i] == u[i - 1]))
+                return fail(sim, KWGB_ERR_ARG, "objective indices must be unique and inside the grid");
+    }
+    int64_t rows = 0, need = 0, max_nt = 1;
+    for (auto& h : sim->hsrc) {
+        rows += h.nsig;
+        need += h.nsig * h.nt;
+        max_nt = std::max(max_nt, h.nt);
+    }
+    if (grad_len < need || (need > 0 && !grad_out)) return fail(sim, KWGB_ERR_ARG, "gradient buffer too small");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sim->last_stream = s;
+
+    // objective points become an internal sensor (p of every step is read from its slots)
+    int32_t osid = -1;
+    if (int e = kwgb_add_sensor(sim, obj_idx, n_obj, KWGB_P_MAX, &osid)) return e;
+    if (int e = freeze(sim)) return e;
+    const int64_t slot0 = sim->hsens[osid].slot0;
+    const size_t N = (size_t)sim->N;
+    const size_t F = N * sizeof(float);
+    const size_t SB = sim->spec_elems * sizeof(float2);
+    const int64_t K = checkpoint_every;
+    const int64_t nck = (n_steps + K - 1) / K;
+    const int64_t segK = std::min(K, n_steps);
+
+    // device memory of the adjoint
+    char* ck = static_cast<char*>(dalloc(sim, (size_t)nck * (6 * F + SB)));
+    char* fin = static_cast<char*>(dalloc(sim, 6 * F + SB));
+    float* seg = static_cast<float*>(dalloc(sim, (size_t)(segK + 1) * 6 * F));
+    float* lam = static_cast<float*>(dalloc(sim, 11 * F));
+    float* pobj = static_cast<float*>(dalloc(sim, (size_t)n_steps * n_obj * sizeof(float)));
+    double* grad = static_cast<double*>(dalloc(sim, (size_t)std::max<int64_t>(rows, 1) * max_nt * sizeof(double)));
+    if (!ck || !fin || !seg || !lam || !pobj || !grad) return fail(sim, KWGB_ERR_OOM, "adjoint buffers");
+    // per signal row: its points and the source scale dt 2 / (3 dx) (the kernel divides by c0)
+    std::vector<int32_t> rptr(1, 0), rnt;
+    std::vector<int64_t> rpts;
+    std::vector<float> rscale;
+    const float sc = (float)(sim->d.dt * 2.0 / (3.0 * sim->d.dx));
+    for (auto& h : sim->hsrc)
+        for (int64_t r = 0; r < h.nsig; ++r) {
+            if (h.nsig == 1) {
+                for (int64_t v : h.idx) { rpts.push_back(v); rscale.push_back(sc); }
+            } else {
+                rpts.push_back(h.idx[r]);
+                rscale.push_back(sc);
+            }
+            rptr.push_back((int32_t)rpts.size());
+            rnt.push_back((int32_t)h.nt);
+        }
+    int64_t* d_obj = nullptr;
+    {
+        std::vector<int64_t> ov(obj_idx, obj_idx + n_obj);
+        if (int e = upload(sim, &d_obj, ov)) return e;
+    }
+    int32_t *d_rptr = nullptr, *d_rnt = nullptr;
+    int64_t* d_rpts = nullptr;
+    float* d_rscale = nullptr;
+    if (rows > 0) {
+        if (int e = upload(sim, &d_rptr, rptr)) return e;
+        if (int e = upload(sim, &d_rnt, rnt)) return e;
+        if (int e = upload(sim, &d_rpts, rpts)) return e;
+        if (int e = upload(sim, &d_rscale, rscale)) return e;
+    }
+    auto save_state = [&](char* dst) -> int {
+        for (int a = 0; a < 3; ++a) {
+            if (int e = copy_dev(sim, dst + a * F, sim->u[a], F, s)) return e;
+            if (int e = copy_dev(sim, dst + (3 + a) * F, sim->rho[a], F, s)) return e;
+        }
+        return copy_dev(sim, dst + 6 * F, sim->P, SB, s);
+    };
+    auto load_state = [&](const char* src, int64_t step) -> int {
+        for (int a = 0; a < 3; ++a) {
+            if (int e = copy_dev(sim, sim->u[a], src + a * F, F, s)) return e;
+            if (int e = copy_dev(sim, sim->rho[a], src + (3 + a) * F, F, s)) return e;
+        }
+        if (int e = copy_dev(sim, sim->P, src + 6 * F, SB, s)) return e;
+        CK(cudaMemcpy(sim->d_step, &step, sizeof(int64_t), cudaMemcpyHostToDevice));
+        return KWGB_OK;
+    };
+    // ---- forward with checkpoints
+    for (int64_t n = 0; n < n_steps; ++n) {
+        if (n % K == 0)
+            if (int e = save_state(ck + (size_t)(n / K) * (6 * F + SB))) return e;
+        if (int e = launch_step(sim, s)) return e;
+        sim->steps++;
+        if (int e = copy_dev(sim, pobj + n * n_obj, sim->sens.p_sens + slot0, n_obj * sizeof(float), s)) return e;
+    }
+    if (int e = save_state(fin)) return e;
+    // sensor accumulators as the forward run left them (the recomputation below steps again)
+    std::vector<std::pair<void*, size_t>> sarr;
+    const SensorC& sc_ = sim->sens;
+    if (sim->n_slots) {
+        sarr.push_back({sc_.p_max, sim->n_slots * sizeof(float)});
+        sarr.push_back({sc_.p2, sim->n_slots * sizeof(double)});
+        sarr.push_back({sc_.p_sens, sim->n_slots * sizeof(float)});
+    }
+    for (int k = 0; k < sc_.nfull; ++k) {
+        sarr.push_back({sc_.full_max[k], N * sizeof(float)});
+        sarr.push_back({sc_.full_p2[k], N * sizeof(double)});
+    }
+    if (sim->n_i) sarr.push_back({sim->I, 3 * sim->n_i * sizeof(double)});
+    size_t sbytes = 0;
+    for (auto& a : sarr) sbytes += a.second;
+    char* snap = static_cast<char*>(dalloc(sim, std::max<size_t>(sbytes, 16)));
+    if (!snap) return fail(sim, KWGB_ERR_OOM, "sensor snapshot");
+    {
+        size_t off = 0;
+        for (auto& a : sarr) {
+            if (int e = copy_dev(sim, snap + off, a.first, a.second, s)) return e;
+            off += a.second;
+        }
+    }
+    // ---- objective value (float64 on the host)
+    std::vector<float> hp((size_t)n_steps * n_obj);
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(hp.data(), pobj, hp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    const double w = 1.0 / ((double)n_obj * (double)n_steps);
+    double J = 0.0;
+    for (float v : hp) J += std::fabs((double)v);
+    *J_out = J * w;
+    // ---- reverse pass
+    CK(cudaMemsetAsync(lam, 0, 11 * F, s));
+    CK(cudaMemsetAsync(grad, 0, (size_t)std::max<int64_t>(rows, 1) * max_nt * sizeof(double), s));
+    AdjFields af{};
+    af.lam_p = lam;
+    for (int a = 0; a < 3; ++a) {
+        af.lam_u[a] = lam + (1 + a) * N;
+        af.lam_rho[a] = lam + (4 + a) * N;
+        af.w[a] = lam + (8 + a) * N;
+    }
+    af.lam_src = lam + 7 * N;
+    const GridC& g = sim->g;
+    auto seg_rho = [&](int64_t k, int a) { return seg + ((size_t)k * 6 + a) * N; };
+    auto seg_u = [&](int64_t k, int a) { return seg + ((size_t)k * 6 + 3 + a) * N; };
+    for (int64_t c = nck - 1; c >= 0; --c) {
+        const int64_t n0 = c * K, n1 = std::min(n0 + K, n_steps);
+        if (int e = load_state(ck + (size_t)c * (6 * F + SB), n0)) return e;
+        for (int64_t n = n0; n < n1; ++n) {
+            for (int a = 0; a < 3; ++a)
+                if (int e = copy_dev(sim, seg_rho(n - n0, a), sim->rho[a], F, s)) return e;
+            if (int e = launch_step(sim, s)) return e;
+            for (int a = 0; a < 3; ++a)
+                if (int e = copy_dev(sim, seg_u(n - n0, a), sim->u[a], F, s)) return e;
+        }
+        for (int a = 0; a < 3; ++a)
+            if (int e = copy_dev(sim, seg_rho(n1 - n0, a), sim->rho[a], F, s)) return e;
+        for (int64_t n = n1 - 1; n >= n0; --n) {
+            const int64_t k = n - n0;
+            LK(launch_adj_obj(n_obj, d_obj, pobj + n * n_obj, w, af.lam_p, s));
+            float* uin[3] = {seg_u(k, 0), seg_u(k, 1), seg_u(k, 2)};
+            if (int e = adj_chain(sim, uin, af.w, Z_DIV, s)) return e;               // d_xi (Eq. 4c)
+            for (int a = 0; a < 3; ++a) {
+                af.rho_before[a] = seg_rho(k, a);
+                af.rho_after[a] = seg_rho(k + 1, a);
+            }
+            LK(launch_adj_dens(g, sim->md, af, s));
+            LK(launch_adj_src((int)rows, d_rptr, d_rpts, d_rscale, d_rnt, af.lam_src, sim->md, grad, max_nt, n, s));
+            if (int e = adj_chain(sim, af.w, af.w, Z_DIV_FWD, s)) return e;          // transpose of Eq. 4c
+            LK(launch_adj_vel(g, sim->md, af, s));
+            if (int e = adj_chain(sim, af.w, af.w, Z_DIV, s)) return e;              // transpose of Eq. 4a
+            LK(launch_adj_psum(g, af, s));
+        }
+    }
+    // ---- put back the forward end state and the sensors
+    if (int e = load_state(fin, n_steps)) return e;
+    {
+        size_t off = 0;
+        for (auto& a : sarr) {
+            if (int e = copy_dev(sim, a.first, snap + off, a.second, s)) return e;
+            off += a.second;
+        }
+    }
+    std::vector<double> hg((size_t)std::max<int64_t>(rows, 1) * max_nt);
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(hg.data(), grad, hg.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    int64_t o = 0, r = 0;
+    for (auto& h : sim->hsrc)
+        for (int64_t q = 0; q < h.nsig; ++q, ++r)
+            for (int64_t n = 0; n < h.nt; ++n) grad_out[o++] = hg[(size_t)r * max_nt + n];
+    sim->adjoint_done = true;
+    return sync_and_flag(sim);
 }
 
 extern "C" int64_t kwgb_device_bytes(const kwgb_sim* sim) { return sim ? sim->bytes : 0; }

@@ -24,7 +24,8 @@
 
 namespace kwgb {
 
-enum { OP_Y_FWD = 0, OP_Y_INV = 1, OP_Z_GRAD_FWD = 2, OP_Z_GRAD_BWD = 3, OP_Z_DIV = 4, OP_Z_ABS = 5 };
+enum { OP_Y_FWD = 0, OP_Y_INV = 1, OP_Z_GRAD_FWD = 2, OP_Z_GRAD_BWD = 3, OP_Z_DIV = 4, OP_Z_ABS = 5,
+       OP_Z_DIV_FWD = 6 };
 
 template <int CX>
 struct TileSmem {
@@ -99,7 +100,7 @@ yz_kernel(const __grid_constant__ YZK a) {
     const int items = nchunk * lines * (ISY ? a.ncomp : 1);
     // loads per tile: compile-time where the operator fixes it, so that values kept
     // for the loads of a tile are provably dead at the end of the tile
-    constexpr int LC = (ISY || OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) ? 1 : (OP == OP_Z_DIV ? 3 : 0);
+    constexpr int LC = (ISY || OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) ? 1 : ((OP == OP_Z_DIV || OP == OP_Z_DIV_FWD) ? 3 : 0);
     const int L = LC ? LC : a.nloads;
     const int my = items > (int)blockIdx.x ? (items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int Q = my * L;
@@ -199,15 +200,15 @@ yz_kernel(const __grid_constant__ YZK a) {
                         for (int m = 0; m < E; ++m) __stcs(out + off + (size_t)(j + TL * m) * es, w[m]);
                     }
                 }
-            } else if (OP == OP_Z_DIV) {
+            } else if (OP == OP_Z_DIV || OP == OP_Z_DIV_FWD) {
                 const int xi = l;
                 const float2 dx = col < g.nh ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
                 const float2 dy = __ldg(g.t.dfy + y);
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
                     float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
-                    d = make_float2(-d.x, d.y);            // Eq. 4c: i k e^{-ikd/2}
-                    v[m] = cscale(cmul(v[m], d), kap[m]);
+                    if (OP == OP_Z_DIV) d = make_float2(-d.x, d.y);   // Eq. 4c: i k e^{-ikd/2}
+                    v[m] = cscale(cmul(v[m], d), kap[m]);            // OP_Z_DIV_FWD: Eq. 4a's operator
                 }
                 line_fft<LOGN, E, +1>(v, j, S, g.t.tw);
                 if (valid) {
@@ -360,7 +361,7 @@ cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, floa
         a.map[0] = in[0]->zmap;
         a.nloads = 1;
         a.load_comp[0] = 0;
-    } else if (kind == Z_DIV) {
+    } else if (kind == Z_DIV || kind == Z_DIV_FWD) {
         for (int i = 0; i < 3; ++i) {
             a.map[i] = in[i]->zmap;
             a.load_comp[i] = i;
@@ -381,6 +382,7 @@ cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, floa
         case Z_GRAD_FWD: return launch_op<OP_Z_GRAD_FWD>(a, g.lognz, items, s);
         case Z_GRAD_BWD: return launch_op<OP_Z_GRAD_BWD>(a, g.lognz, items, s);
         case Z_DIV: return launch_op<OP_Z_DIV>(a, g.lognz, items, s);
+        case Z_DIV_FWD: return launch_op<OP_Z_DIV_FWD>(a, g.lognz, items, s);
         case Z_ABS: return launch_op<OP_Z_ABS>(a, g.lognz, items, s);
     }
     return cudaErrorInvalidValue;

@@ -93,10 +93,11 @@ struct StepC {
 cudaError_t launch_y_pass(const GridC& g, int dir, const SpecBuf* const* in, float2* const* out,
                           int ncomp, int* flag, cudaStream_t s);
 
-enum ZOpKind { Z_GRAD_FWD = 0, Z_GRAD_BWD = 1, Z_DIV = 2, Z_ABS = 3 };
+enum ZOpKind { Z_GRAD_FWD = 0, Z_GRAD_BWD = 1, Z_DIV = 2, Z_ABS = 3, Z_DIV_FWD = 4 };
 // z forward FFT -> operator -> z inverse FFT:
 //   Z_GRAD_*: in[0] -> out[xi] (NULL skips a component)
 //   Z_DIV:    in[xi] -> out[xi]  (Eq. 4c operator)
+//   Z_DIV_FWD: in[xi] -> out[xi] (Eq. 4a operator per component; adjoint pass)
 //   Z_ABS:    in[0] -> out[0] with k^{y-2}, in[1] -> out[1] with k^{y-1} (NULL skips)
 cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, float2* const* out,
                         int* flag, cudaStream_t s);
@@ -149,5 +150,29 @@ cudaError_t launch_intensity_accum(int64_t n, const int64_t* idx, const GridC& g
                                    const float* p_sens, const int32_t* slot, double* I,
                                    const int64_t* step, int skip_first, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t s);
+
+// ---- adjoint (reverse-mode) pointwise kernels --------------------------
+struct AdjFields {
+    float* lam_p;             // lambda of p^{n+1} (in), later of p^n
+    float* lam_u[3];          // lambda of u^{n+1/2} -> of u^{n-1/2}
+    float* lam_rho[3];        // lambda of rho_xi^{n+1} -> of rho_xi^n
+    float* lam_src;           // sum_xi lambda of rho_xi^{n+1} (source gradient)
+    float* w[3];              // work: d_xi -> lambda_d_xi -> (Eq. 4a op) -> lambda_g_xi -> ...
+    const float* rho_before[3];
+    const float* rho_after[3];
+};
+// Eq. 6 and Eq. 4d backwards (lossless): lambda_rho_xi, lambda_d_xi (into w), lambda_src
+cudaError_t launch_adj_dens(const GridC& g, const Medium& m, const AdjFields& a, cudaStream_t s);
+// Eq. 4b backwards: w holds D_f lambda_d on entry and lambda_g on exit; lambda_u updated
+cudaError_t launch_adj_vel(const GridC& g, const Medium& m, const AdjFields& a, cudaStream_t s);
+// lambda_p = -(w0 + w1 + w2)
+cudaError_t launch_adj_psum(const GridC& g, const AdjFields& a, cudaStream_t s);
+// lambda_p[idx_k] += weight * sign(p_k) for the objective points
+cudaError_t launch_adj_obj(int64_t n, const int64_t* idx, const float* p, double weight, float* lam_p,
+                           cudaStream_t s);
+// per signal row r: grad[r * stride + n] += sum over its points of lambda_src * scale / c0 (n < nt_r)
+cudaError_t launch_adj_src(int rows, const int32_t* row_ptr, const int64_t* pts, const float* scale,
+                           const int32_t* nt, const float* lam_src, const Medium& m, double* grad,
+                           int64_t stride, int64_t n, cudaStream_t s);
 
 }  // namespace kwgb

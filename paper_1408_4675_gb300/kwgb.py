@@ -82,6 +82,8 @@ def load():
     L.kwgb_step_profiled.restype = ctypes.c_int
     L.kwgb_kernel_name.argtypes = [i32]
     L.kwgb_kernel_name.restype = ctypes.c_char_p
+    L.kwgb_adjoint.argtypes = [vp, vp, i64, ctypes.c_int, i64, i64, ctypes.POINTER(ctypes.c_double), vp, i64, vp]
+    L.kwgb_adjoint.restype = ctypes.c_int
     L.kwgb_destroy.argtypes = [vp]
     L.kwgb_destroy.restype = None
     for name in ("kwgb_create", "kwgb_set_allocator", "kwgb_set_medium", "kwgb_set_initial_pressure",
@@ -136,6 +138,7 @@ class Simulation:
         self.h = h
         self._cb = None
         self._sensors = []
+        self._src_shapes = []
         if use_torch_allocator:
             self._use_torch_allocator()
 
@@ -207,6 +210,7 @@ class Simulation:
         sid = ctypes.c_int32()
         self._check(self.L.kwgb_add_source(self.h, _ptr(idx), idx.size, _ptr(sig), sig.shape[0],
                                            sig.shape[1], mode, ctypes.byref(sid)))
+        self._src_shapes.append(sig.shape)
         return sid.value
 
     def add_sensor(self, idx=None, record=P_MAX):
@@ -259,6 +263,22 @@ class Simulation:
         self._check(self.L.kwgb_step_profiled(self.h, _stream_ptr(stream), _ptr(kinds), _ptr(ms),
                                               cap, ctypes.byref(n)))
         return [(self.L.kwgb_kernel_name(int(kinds[i])).decode(), float(ms[i])) for i in range(n.value)]
+
+    def adjoint(self, obj_idx, n_steps, checkpoint_every=50, stream=None):
+        """Run n_steps forward and the adjoint; returns (J, [dJ/dsignal per
+        source, shaped (n_signals, n_t)]) for J = mean |p| over obj_idx."""
+        obj = np.ascontiguousarray(np.asarray(obj_idx, dtype=np.int64))
+        shapes = [tuple(s) for s in self._src_shapes]
+        total = sum(a * b for a, b in shapes)
+        g = np.zeros(max(total, 1), dtype=np.float64)
+        J = ctypes.c_double()
+        self._check(self.L.kwgb_adjoint(self.h, _ptr(obj), obj.size, 0, int(n_steps), int(checkpoint_every),
+                                        ctypes.byref(J), _ptr(g), g.size, _stream_ptr(stream)))
+        out, o = [], 0
+        for a, b in shapes:
+            out.append(g[o:o + a * b].reshape(a, b))
+            o += a * b
+        return J.value, out
 
     def status(self):
         return self.L.kwgb_status(self.h)
