@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--n", type=int, default=None,
                     help="cubic grid size override (same recipe; for profiling small cases)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 1024^3 step and the adjoint measurements")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -302,6 +304,9 @@ def run_ours(args):
 
     if not args.no_e2e:
         out["e2e"] = e2e(args, cfg, kwgb, torch)
+    if not args.no_extra and args.config == 3 and args.n is None:
+        out["also_1024"] = step_1024(args, kwgb, torch)
+        out["adjoint"] = adjoint_measure(kwgb, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
         s, cores = oracle_sample(args.config, 128, 6)
         cpu_ms = 1e3 * s * scale_to(128, cfg["shape"][0])
@@ -312,6 +317,57 @@ def run_ours(args):
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def step_1024(args, kwgb, torch):
+    """The 1024^3 workload (same bowl and tissue recipe at 0.1 mm): ms/step and
+    the step roofline fraction, timed like the main line."""
+    cfg = inputs.make_config(4, n_steps=args.warmup + args.steps + 8)
+    sim, _ = kwgb.from_config(cfg)
+    stream = torch.cuda.current_stream()
+    sim.step(args.warmup, stream)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = {}
+    for name, t in sim.step_profiled(stream):
+        prof[name] = prof.get(name, 0.0) + t
+    bytes_ = sum(kernel_bytes(cfg).get(k, 0) for k in prof)
+    peak, _ = measured_peaks()
+    res = {"workload": workload_name(cfg), "ms_per_step": round(ms, 3),
+           "bytes_per_step": bytes_, "frac": round(bytes_ / (ms * 1e-3) / 1e9 / peak, 4),
+           "device_gb": round(sim.device_bytes / 1e9, 2), "status": sim.status(),
+           "kernels_ms": {k: round(v, 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1])}}
+    sim.close()
+    return res
+
+
+def adjoint_measure(kwgb, torch):
+    """Forward + hand-written adjoint of the 256-element segmented bowl at 128^3
+    (600 steps, checkpoint every 50): time per step and device memory, beside
+    the plain forward step of the same problem."""
+    from paper_1408_4675_gb300.autograd import FocalProblem
+    cfg = inputs.make_config(5)
+    prob = FocalProblem(cfg, checkpoint_every=50)
+    sim = prob.simulation(cfg["phases"], cfg["amps"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(prob.n_steps)
+    sim.status()
+    fwd = (time.perf_counter() - t0) * 1e3 / prob.n_steps
+    sim.close()
+    t0 = time.perf_counter()
+    J, dphi, damp, _ = prob.value_and_grad(cfg["phases"], cfg["amps"])
+    tot = (time.perf_counter() - t0) * 1e3 / prob.n_steps
+    return {"workload": "segmented_bowl_256_elements_128^3", "steps": prob.n_steps, "checkpoint_every": 50,
+            "forward_ms_per_step": round(fwd, 4), "forward_plus_adjoint_ms_per_step": round(tot, 4),
+            "device_gb": round(prob.last_device_bytes / 1e9, 3), "J": J,
+            "grad_norm_phases": float(np.linalg.norm(dphi))}
 
 
 def e2e(args, cfg, kwgb, torch):

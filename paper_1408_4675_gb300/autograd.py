@@ -29,6 +29,7 @@ class FocalProblem:
         self.n_steps = int(n_steps or cfg["n_steps"])
         self.checkpoint_every = int(checkpoint_every)
         self.t = (np.arange(self.n_steps) + 0.5) * cfg["dt"]
+        self.last_device_bytes = 0
 
     def signals(self, phases, amps):
         w = 2.0 * np.pi * self.freq
@@ -59,6 +60,7 @@ class FocalProblem:
     def value_and_grad(self, phases, amps):
         sim = self.simulation(phases, amps)
         J, g = sim.adjoint(self.focal, self.n_steps, self.checkpoint_every)
+        self.last_device_bytes = sim.device_bytes
         sim.close()
         w = 2.0 * np.pi * self.freq
         dphi = np.array([(gr[0] * a * np.cos(w * self.t + ph)).sum() for gr, a, ph in zip(g, amps, phases)])

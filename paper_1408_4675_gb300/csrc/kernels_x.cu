@@ -32,6 +32,9 @@ struct XShape {
     static constexpr int E = M >= 512 ? 16 : (M >= 8 ? 8 : M);
     static constexpr int TL = M / E;
     static_assert(TL <= 32, "a row must fit in one warp");
+    // resident CTAs per SM the fused kernels are compiled for: 1024-wide rows
+    // (16 values per thread) get the full register file instead of spilling
+    static constexpr int MINB = LOGM >= 9 ? 1 : 2;
     static constexpr int RPB = XTHREADS / TL;        // rows per CTA
     static constexpr int PITCH = M + M / 16 + 2;     // complex slots per row (padded, + Nyquist)
     static constexpr int SMEM = RPB * PITCH * (int)sizeof(float2);
@@ -248,7 +251,7 @@ struct XVelK {
 };
 
 template <int LOGM, int MODE>
-__global__ void __launch_bounds__(XTHREADS, 2) x_vel_kernel(const XVelK K) {
+__global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_vel_kernel(const XVelK K) {
     using Sh = XShape<LOGM>;
     constexpr int E = Sh::E, TL = Sh::TL;
     extern __shared__ float2 smem[];
@@ -325,7 +328,7 @@ struct XDensK {
 
 
 template <int LOGM, bool FUSED_EOS>
-__global__ void __launch_bounds__(XTHREADS, 2) x_dens_kernel(const XDensK K) {
+__global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(const XDensK K) {
     using Sh = XShape<LOGM>;
     using St = XStage<LOGM>;
     constexpr int E = Sh::E, TL = Sh::TL, RPW = St::RPW, WPB = XTHREADS / 32;
@@ -476,7 +479,7 @@ struct XEosK {
 };
 
 template <int LOGM>
-__global__ void __launch_bounds__(XTHREADS, 2) x_eos_kernel(const XEosK K) {
+__global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_eos_kernel(const XEosK K) {
     using Sh = XShape<LOGM>;
     constexpr int E = Sh::E, TL = Sh::TL;
     extern __shared__ float2 smem[];
