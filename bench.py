@@ -305,7 +305,9 @@ def run_ours(args):
     if not args.no_e2e:
         out["e2e"] = e2e(args, cfg, kwgb, torch)
     if not args.no_extra and args.config == 3 and args.n is None:
-        out["also_1024"] = step_1024(args, kwgb, torch)
+        out["mixed_f16"] = step_variant(args, kwgb, torch, 3, 8)
+        out["mixed_bf16"] = step_variant(args, kwgb, torch, 3, 4)
+        out["also_1024"] = step_variant(args, kwgb, torch, 4, 0)
         out["adjoint"] = adjoint_measure(kwgb, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
         s, cores = oracle_sample(args.config, 128, 6)
@@ -319,10 +321,12 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def step_1024(args, kwgb, torch):
-    """The 1024^3 workload (same bowl and tissue recipe at 0.1 mm): ms/step and
-    the step roofline fraction, timed like the main line."""
-    cfg = inputs.make_config(4, n_steps=args.warmup + args.steps + 8)
+def step_variant(args, kwgb, torch, cfg_id, extra_flags):
+    """Another workload or form, timed like the main line: the 1024^3 workload
+    (same bowl and tissue recipe at 0.1 mm), or the bfloat16-split
+    tensor-core form (extra_flags = 4) of the 512^3 workload."""
+    cfg = inputs.make_config(cfg_id, n_steps=args.warmup + args.steps + 8)
+    cfg["flags"] = cfg["flags"] | extra_flags
     sim, _ = kwgb.from_config(cfg)
     stream = torch.cuda.current_stream()
     sim.step(args.warmup, stream)
@@ -339,7 +343,9 @@ def step_1024(args, kwgb, torch):
         prof[name] = prof.get(name, 0.0) + t
     bytes_ = sum(kernel_bytes(cfg).get(k, 0) for k in prof)
     peak, _ = measured_peaks()
-    res = {"workload": workload_name(cfg), "ms_per_step": round(ms, 3),
+    form = {4: "bf16-split tensor-core y/z stages", 8: "f16-split tensor-core y/z stages"}.get(extra_flags, "float32")
+    res = {"workload": workload_name(cfg), "form": form,
+           "ms_per_step": round(ms, 3),
            "bytes_per_step": bytes_, "frac": round(bytes_ / (ms * 1e-3) / 1e9 / peak, 4),
            "device_gb": round(sim.device_bytes / 1e9, 2), "status": sim.status(),
            "kernels_ms": {k: round(v, 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1])}}

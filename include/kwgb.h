@@ -49,6 +49,8 @@ extern "C" {
 /* ---- grid flags (kwgb_grid_desc.flags) ---------------------------------- */
 #define KWGB_NONLINEAR   1u  /* Eq. 4d denominator and (B/2A) rho^2/rho0 of Eq. 6 */
 #define KWGB_ABSORBING   2u  /* power-law absorption/dispersion L_d of Eq. 8     */
+#define KWGB_MIXED_BF16  4u  /* y/z FFT stages as bfloat16-split tensor-core products (radix 8, float32 accumulation); needs ny, nz >= 16 */
+#define KWGB_MIXED_F16   8u  /* same with float16 hi + lo and a per-column power-of-two scale; needs ny, nz >= 16 */
 
 /* ---- sensor outputs (kwgb_add_sensor record / kwgb_read which) ---------- */
 #define KWGB_P_MAX  1u   /* max_n p^n, n = 1..Nt                               */
@@ -93,7 +95,7 @@ typedef struct kwgb_sim kwgb_sim;  /* opaque; owned by the library */
  *   pml_alpha     PML strength per axis [Np per grid point]; the absorption is
  *                 alpha * (c_ref/dxi) * (depth/size)^4, depth measured in cells
  *                 from the inner edge of the layer
- *   flags         KWGB_NONLINEAR | KWGB_ABSORBING
+ *   flags         KWGB_NONLINEAR | KWGB_ABSORBING, optionally one of KWGB_MIXED_BF16 / KWGB_MIXED_F16
  *   alpha_power   power-law exponent y (Eq. 3), 0 < y < 3, y != 1; one value
  *                 for the whole grid                                          */
 typedef struct {

@@ -177,7 +177,12 @@ extern "C" int kwgb_create(const kwgb_grid_desc* desc, kwgb_sim** out) {
     }
     if (!(desc->dt > 0) || !std::isfinite(desc->dt)) return bad(KWGB_ERR_ARG, "dt must be positive");
     if (!(desc->c_ref > 0) || !std::isfinite(desc->c_ref)) return bad(KWGB_ERR_ARG, "c_ref must be positive");
-    if (desc->flags & ~(KWGB_NONLINEAR | KWGB_ABSORBING)) return bad(KWGB_ERR_ARG, "unknown flag bits");
+    if (desc->flags & ~(KWGB_NONLINEAR | KWGB_ABSORBING | KWGB_MIXED_BF16 | KWGB_MIXED_F16))
+        return bad(KWGB_ERR_ARG, "unknown flag bits");
+    if ((desc->flags & KWGB_MIXED_BF16) && (desc->flags & KWGB_MIXED_F16))
+        return bad(KWGB_ERR_ARG, "choose one tensor-core form");
+    if ((desc->flags & (KWGB_MIXED_BF16 | KWGB_MIXED_F16)) && (desc->ny < 16 || desc->nz < 16))
+        return bad(KWGB_ERR_UNSUPPORTED, "the tensor-core form needs ny, nz >= 16");
     if (desc->flags & KWGB_ABSORBING) {
         const double y = desc->alpha_power;
         if (!(y > 0 && y < 3) || y == 1.0) return bad(KWGB_ERR_ARG, "alpha_power must be in (0,3), != 1");
@@ -210,6 +215,7 @@ extern "C" int kwgb_create(const kwgb_grid_desc* desc, kwgb_sim** out) {
     md.tan_pi_y_2 = (float)std::tan(kPi * y / 2.0);
     md.nonlinear = (desc->flags & KWGB_NONLINEAR) ? 1 : 0;
     md.absorbing = (desc->flags & KWGB_ABSORBING) ? 1 : 0;
+    g.mixed = (desc->flags & KWGB_MIXED_BF16) ? 1 : ((desc->flags & KWGB_MIXED_F16) ? 2 : 0);
     *out = sim;
     return KWGB_OK;
 }

@@ -1,0 +1,242 @@
+// Split-precision tensor-core form of the strided FFT passes.
+//
+// A tile (CX columns x N points, layout [e][c] in shared memory) is
+// transformed in place.  Every radix-8 Stockham stage is written as a real
+// matrix product on the tensor cores: the 8-point complex DFT in real form is
+// the 16 x 16 matrix
+//     W = [[C, -S], [S, C]],  C + iS = exp(DIR 2 pi i r k / 8),
+// acting on columns [Re x_0..Re x_7, Im x_0..Im x_7] of 8 butterflies at a
+// time (mma.sync m16n8k16: W as the A operand, the butterflies as B, float32
+// accumulation).  Both operands are split into bfloat16 hi + lo parts
+// (hi = bf16(v), lo = bf16(v - hi)) and the product is formed as
+// W_hi X_hi + W_hi X_lo + W_lo X_hi, which keeps about 16 significant bits of
+// every operand (the dropped W_lo X_lo term is of relative size 2^-16).
+// PREC 2 uses float16 hi + lo instead (11 + 11 significant bits, relative
+// residue 2^-22): float16 has a narrow exponent range, so each column is
+// scaled by a power of two (exact) that brings its largest input to [32, 64);
+// 8-point stages grow values at most 8x, so a 512-point column stays below
+// the float16 maximum 65504; outputs are scaled back before they are stored.
+// A remaining radix-2 or radix-4 stage runs in float32 on the CUDA cores.
+// Each thread reads its B fragment (two complex inputs of one butterfly)
+// straight from the Stockham input positions, applies the stage twiddles, and
+// writes its D fragment (one complex output of two butterflies) straight to
+// the Stockham output positions, so no extra shuffles are needed.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fft_core.cuh"
+
+namespace kwgb {
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_half, float hi_half) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo_half, hi_half);   // .x in the low 16 bits
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// split a pair (a, b) into packed bf16 hi and lo words
+__device__ __forceinline__ void split_bf16(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    const float ra = a - __bfloat162float(ha), rb = b - __bfloat162float(hb);
+    __nv_bfloat162 h;
+    h.x = ha;
+    h.y = hb;
+    hi = *reinterpret_cast<uint32_t*>(&h);
+    lo = pack_bf16(ra, rb);
+}
+
+// split a pair (a, b) into packed float16 hi and lo words
+__device__ __forceinline__ void split_f16(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+    const float ra = a - __half2float(ha), rb = b - __half2float(hb);
+    __half2 h;
+    h.x = ha;
+    h.y = hb;
+    hi = *reinterpret_cast<uint32_t*>(&h);
+    __half2 l = __floats2half2_rn(ra, rb);
+    lo = *reinterpret_cast<uint32_t*>(&l);
+}
+
+template <int PREC>
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    if constexpr (PREC == 2) split_f16(a, b, hi, lo);
+    else split_bf16(a, b, hi, lo);
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    if constexpr (PREC == 2) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+            "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    } else {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+            "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
+}
+
+// A fragments (hi and lo) of the real 16 x 16 DFT-8 matrix for this lane:
+// reg0 (row g, cols 2t, 2t+1) = C, reg1 (row g+8) = S, reg2 (row g, cols 2t+8..) = -S,
+// reg3 (row g+8, cols 2t+8..) = C, with C + iS = exp(DIR 2 pi i g k / 8).
+template <int DIR, int PREC>
+__device__ __forceinline__ void dft8_matrix(int lane, uint32_t (&ah)[4], uint32_t (&al)[4]) {
+    const int g = lane >> 2, t = lane & 3;
+    float c[2], s[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int m = (2 * g * (2 * t + i)) & 15;             // 2 pi g k / 8 = 2 pi (2 g k) / 16
+        c[i] = cos16(m);
+        s[i] = DIR > 0 ? sin16(m) : -sin16(m);
+    }
+    split2<PREC>(c[0], c[1], ah[0], al[0]);
+    split2<PREC>(s[0], s[1], ah[1], al[1]);
+    split2<PREC>(-s[0], -s[1], ah[2], al[2]);
+    split2<PREC>(c[0], c[1], ah[3], al[3]);
+}
+
+// One radix-8 Stockham stage (stride NS) of a tile, on the tensor cores.
+// Butterfly beta = 32 w + 8 G + n (column c = beta % CX, butterfly b = beta / CX).
+template <int N, int CX, int NS, int DIR, int THREADS, int PREC>
+__device__ __forceinline__ void tc_stage8(float2* buf, const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                          const float2* __restrict__ tw, const float* colscale) {
+    constexpr int NBF = CX * N / 8;                           // butterflies in the tile
+    constexpr int WARPS = THREADS / 32;
+    constexpr int GROUPS = NBF / (8 * WARPS);                 // 8-butterfly groups per warp
+    static_assert(NBF % (8 * WARPS) == 0, "tile / warp split");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    float d[GROUPS][4];
+#pragma unroll
+    for (int G = 0; G < GROUPS; ++G) {
+        const int beta = (w * GROUPS + G) * 8 + g;            // this lane's B column
+        const int c = beta % CX, b = beta / CX;
+        float2 x0 = buf[(b + (2 * t) * (N / 8)) * CX + c];
+        float2 x1 = buf[(b + (2 * t + 1) * (N / 8)) * CX + c];
+        if (NS > 1) {
+            const int k = b & (NS - 1);
+            x0 = cmul(x0, twiddle1024<DIR>(tw, k * (2 * t) * (1024 / (NS * 8))));
+            x1 = cmul(x1, twiddle1024<DIR>(tw, k * (2 * t + 1) * (1024 / (NS * 8))));
+        }
+        if (PREC == 2) {
+            const float sc = colscale[c];
+            x0 = cscale(x0, sc);
+            x1 = cscale(x1, sc);
+        }
+        uint32_t bh0, bl0, bh1, bl1;
+        split2<PREC>(x0.x, x1.x, bh0, bl0);                   // rows 2t, 2t+1: real parts
+        split2<PREC>(x0.y, x1.y, bh1, bl1);                   // rows 2t+8, 2t+9: imaginary parts
+        d[G][0] = d[G][1] = d[G][2] = d[G][3] = 0.f;
+        mma_16816<PREC>(d[G], al, bh0, bh1);
+        mma_16816<PREC>(d[G], ah, bl0, bl1);
+        mma_16816<PREC>(d[G], ah, bh0, bh1);
+    }
+    __syncthreads();                                          // all inputs read
+#pragma unroll
+    for (int G = 0; G < GROUPS; ++G) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {                         // output g of butterflies 2t, 2t+1
+            const int beta = (w * GROUPS + G) * 8 + 2 * t + i;
+            const int c = beta % CX, b = beta / CX;
+            const int base = (b / NS) * NS * 8 + (b & (NS - 1));
+            const float us = PREC == 2 ? 1.0f / colscale[c] : 1.0f;           // exact: a power of two
+            buf[(base + g * NS) * CX + c] = make_float2(d[G][i] * us, d[G][2 + i] * us);
+        }
+    }
+    __syncthreads();
+}
+
+// A float32 radix-RP Stockham stage (RP = 2 or 4) on the tile in shared memory.
+template <int N, int CX, int RP, int NS, int DIR, int THREADS>
+__device__ __forceinline__ void f32_stage(float2* buf, const float2* __restrict__ tw) {
+    constexpr int NBF = CX * N / RP;
+    float2 o[(NBF + THREADS - 1) / THREADS][RP];
+#pragma unroll
+    for (int q = 0; q < (NBF + THREADS - 1) / THREADS; ++q) {
+        const int beta = threadIdx.x + q * THREADS;
+        if (beta < NBF) {
+            const int c = beta % CX, b = beta / CX;
+            float2 v[RP];
+#pragma unroll
+            for (int r = 0; r < RP; ++r) v[r] = buf[(b + r * (N / RP)) * CX + c];
+            if (NS > 1) {
+                const int k = b & (NS - 1);
+#pragma unroll
+                for (int r = 1; r < RP; ++r) v[r] = cmul(v[r], twiddle1024<DIR>(tw, k * r * (1024 / (NS * RP))));
+            }
+            dft_reg<RP, DIR>(v);
+#pragma unroll
+            for (int r = 0; r < RP; ++r) o[q][r] = v[r];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < (NBF + THREADS - 1) / THREADS; ++q) {
+        const int beta = threadIdx.x + q * THREADS;
+        if (beta < NBF) {
+            const int c = beta % CX, b = beta / CX;
+            const int base = (b / NS) * NS * RP + (b & (NS - 1));
+#pragma unroll
+            for (int r = 0; r < RP; ++r) buf[(base + r * NS) * CX + c] = o[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Radix-8 tensor-core stages while they fit, then one float32 stage of the rest.
+template <int LOGN, int CX, int DIR, int THREADS, int PREC, int NS>
+struct TcChain {
+    __device__ __forceinline__ static void run(float2* buf, const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                               const float2* __restrict__ tw, const float* colscale) {
+        constexpr int N = 1 << LOGN;
+        constexpr int REM = N / NS;
+        if constexpr (REM >= 8) {
+            tc_stage8<N, CX, NS, DIR, THREADS, PREC>(buf, ah, al, tw, colscale);
+            TcChain<LOGN, CX, DIR, THREADS, PREC, NS * 8>::run(buf, ah, al, tw, colscale);
+        } else {
+            f32_stage<N, CX, (REM >= 4 ? 4 : 2), NS, DIR, THREADS>(buf, tw);
+        }
+    }
+};
+template <int LOGN, int CX, int DIR, int THREADS, int PREC>
+struct TcChain<LOGN, CX, DIR, THREADS, PREC, (1 << LOGN)> {
+    __device__ __forceinline__ static void run(float2*, const uint32_t (&)[4], const uint32_t (&)[4],
+                                               const float2*, const float*) {}
+};
+
+// In-place unnormalised DFT of every column of the tile (natural order in and out).
+// Starts and ends with the tile fully written (callers synchronise before).
+// colscale: CX floats of shared memory (used by PREC 2).
+template <int LOGN, int CX, int DIR, int THREADS, int PREC>
+__device__ __forceinline__ void tile_fft_tc(float2* buf, const float2* __restrict__ tw, float* colscale) {
+    uint32_t ah[4], al[4];
+    dft8_matrix<DIR, PREC>(threadIdx.x & 31, ah, al);
+    if constexpr (PREC == 2) {
+        // per column: largest |Re|, |Im| -> power-of-two scale to [32, 64)
+        constexpr int N = 1 << LOGN;
+        unsigned int* cm = reinterpret_cast<unsigned int*>(colscale);
+        if (threadIdx.x < CX) cm[threadIdx.x] = 0u;
+        __syncthreads();
+        for (int i = threadIdx.x; i < N * CX; i += THREADS) {
+            const float2 v = buf[i];
+            const float m = fmaxf(fabsf(v.x), fabsf(v.y));
+            atomicMax(cm + (i % CX), __float_as_uint(m));      // non-negative floats order as integers
+        }
+        __syncthreads();
+        if (threadIdx.x < CX) {
+            const float m = __uint_as_float(cm[threadIdx.x]);
+            int e = 0;
+            if (m > 0.f && isfinite(m)) frexpf(m, &e);          // m = f 2^e, f in [0.5, 1)
+            colscale[threadIdx.x] = (m > 0.f && isfinite(m)) ? ldexpf(1.0f, 6 - e) : 1.0f;
+        }
+        __syncthreads();
+    }
+    TcChain<LOGN, CX, DIR, THREADS, PREC, 1>::run(buf, ah, al, tw, colscale);
+}
+
+}  // namespace kwgb

@@ -1,244 +1,9 @@
-// Strided-axis FFT passes on the half spectra [nz][ny][nhp] (complex64).
-//
-// Work item = a tile of CX consecutive x-columns times one whole line along
-// y (y pass) or z (z pass).  The kernels are persistent: each CTA walks its
-// share of the tiles with a two-stage shared-memory ring that the TMA unit
-// fills (cp.async.bulk.tensor, box CX x 256 lines, completion on an
-// mbarrier), so the HBM reads of tile t+1 run while tile t is transformed.
-// The x extent of the tensor map is nh (not the padded pitch), so the ragged
-// last tile reads no padding: the TMA zero-fills those columns.
-//
-// Thread (c, j) takes elements j + TL*m of column c into registers; the
-// Stockham passes exchange through the stage buffer the tile arrived in, and
-// results are stored from registers (a warp writes whole 64..128-byte row
-// segments).
-//
-// The z pass is the fused spectral-operator pass: forward z FFT, the
-// pointwise operator of Eq. 4a, 4c or 8 (all of kx, ky, kz are known here),
-// inverse z FFT, store.  It plays the role of the paper's transposed-space
-// spectral multiply (Sec. 3.2): the spectrum does not return to HBM between
-// the forward and the inverse transform along z.
-#include "fft_core.cuh"
-#include "kwgb_internal.h"
-#include "tma.cuh"
+// Host side of the strided-axis passes: tensor-map encoding and launch
+// dispatch (the kernels are in yz_kernel.cuh, instantiated per precision form
+// in yz_f32.cu, yz_bf16.cu and yz_f16.cu).
+#include "yz_kernel.cuh"
 
 namespace kwgb {
-
-enum { OP_Y_FWD = 0, OP_Y_INV = 1, OP_Z_GRAD_FWD = 2, OP_Z_GRAD_BWD = 3, OP_Z_DIV = 4, OP_Z_ABS = 5,
-       OP_Z_DIV_FWD = 6 };
-
-template <int CX>
-struct TileSmem {
-    float2* buf;
-    int c;
-    __device__ __forceinline__ float2& at(int e) { return buf[e * CX + c]; }
-    __device__ __forceinline__ void sync() { __syncthreads(); }
-};
-
-template <int LOGN, bool ISY>
-struct TShape {
-    static constexpr int N = 1 << LOGN;
-    static constexpr int E = ISY ? (LOGN >= 8 ? 16 : 8) : 8;   // z: E = 8 keeps the operator pass spill-free
-    static constexpr int TL = N / E;
-    static constexpr int MAXT = 512;
-    static constexpr int CX = (MAXT / TL) >= 16 ? 16 : (MAXT / TL);
-    static constexpr int THREADS = CX * TL;
-    static constexpr int BOX = N < 256 ? N : 256;
-    static constexpr int NBOX = N / BOX;
-    static constexpr int STAGE = N * CX;                       // complex elements per stage
-    static constexpr int SMEM = 2 * STAGE * (int)sizeof(float2) + 64;
-};
-
-struct alignas(64) YZK {
-    CUtensorMap map[3];       // input tensor maps (box of the pass)
-    GridC g;
-    float2* out[3];
-    int ncomp;                // y pass: components (items carry the component)
-    int nloads;               // z pass: loads per item
-    int load_comp[3];         // z pass: component of each load
-    int* flag;
-};
-
-// sinc(x) = sin(x)/x with sinc(0) = 1 (kappa of Sec. 2.2).  For |x| <= 3 the
-// Taylor series sum_n (-x^2)^n / (2n+1)! up to n = 9 is used (branch-free; the
-// truncation error is below the n = 10 term, 3^20/21! < 7e-11); beyond that
-// sin(x)/x directly.
-__device__ __forceinline__ float sinc_f(float x) {
-    const float x2 = x * x;
-    if (x2 > 9.0f) return __fdividef(sinf(x), x);
-    float p = -1.0f / 121645100408832000.0f;          // -1/19!
-    p = fmaf(p, x2, 1.0f / 355687428096000.0f);       //  1/17!
-    p = fmaf(p, x2, -1.0f / 1307674368000.0f);        // -1/15!
-    p = fmaf(p, x2, 1.0f / 6227020800.0f);            //  1/13!
-    p = fmaf(p, x2, -1.0f / 39916800.0f);             // -1/11!
-    p = fmaf(p, x2, 1.0f / 362880.0f);                //  1/9!
-    p = fmaf(p, x2, -1.0f / 5040.0f);                 // -1/7!
-    p = fmaf(p, x2, 1.0f / 120.0f);                   //  1/5!
-    p = fmaf(p, x2, -1.0f / 6.0f);                    // -1/3!
-    return fmaf(p, x2, 1.0f);
-}
-
-// a.out[i] for a run-time i without copying the parameter array to local memory
-__device__ __forceinline__ float2* out_ptr(const YZK& a, int i) {
-    return i == 0 ? a.out[0] : (i == 1 ? a.out[1] : a.out[2]);
-}
-
-template <int LOGN, int OP>
-__global__ void __launch_bounds__(TShape<LOGN, (OP < 2)>::THREADS, (OP < 2) ? 1 : 2)
-yz_kernel(const __grid_constant__ YZK a) {
-    constexpr bool ISY = OP < 2;
-    using Sh = TShape<LOGN, ISY>;
-    constexpr int E = Sh::E, TL = Sh::TL, CX = Sh::CX, STAGE = Sh::STAGE;
-    extern __shared__ __align__(128) float2 smem[];
-    __shared__ int abort_flag;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
-    const GridC& g = a.g;
-    const int tid = threadIdx.x;
-    const int c = tid % CX, j = tid / CX;
-    const int nchunk = (g.nh + CX - 1) / CX;
-    const int lines = ISY ? g.nz : g.ny;
-    const int items = nchunk * lines * (ISY ? a.ncomp : 1);
-    // loads per tile: compile-time where the operator fixes it, so that values kept
-    // for the loads of a tile are provably dead at the end of the tile
-    constexpr int LC = (ISY || OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) ? 1 : ((OP == OP_Z_DIV || OP == OP_Z_DIV_FWD) ? 3 : 0);
-    const int L = LC ? LC : a.nloads;
-    const int my = items > (int)blockIdx.x ? (items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int Q = my * L;
-
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-        abort_flag = 0;
-    }
-    __syncthreads();
-
-    auto issue = [&](int q) {                 // thread 0 only
-        const int item = (int)blockIdx.x + (q / L) * (int)gridDim.x;
-        const int l = q % L;
-        const int chunk = item % nchunk;
-        const int line = (item / nchunk) % lines;
-        const int mi = ISY ? item / (nchunk * lines) : (l == 0 ? a.load_comp[0] : (l == 1 ? a.load_comp[1] : a.load_comp[2]));
-        const CUtensorMap* map = mi == 0 ? &a.map[0] : (mi == 1 ? &a.map[1] : &a.map[2]);
-        float2* dst = smem + (q & 1) * STAGE;
-        uint64_t* b = &bar[q & 1];
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(b, STAGE * (uint32_t)sizeof(float2));
-#pragma unroll
-        for (int k = 0; k < Sh::NBOX; ++k) {
-            if (ISY) tma_load_3d(dst + k * Sh::BOX * CX, map, chunk * CX, k * Sh::BOX, line, b);
-            else tma_load_3d(dst + k * Sh::BOX * CX, map, chunk * CX, line, k * Sh::BOX, b);
-        }
-    };
-
-    if (tid == 0 && Q > 0) issue(0);
-    float kap[E];
-    float lg[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) { kap[m] = 0.f; lg[m] = 0.f; }
-
-    for (int q = 0; q < Q; ++q) {
-        const int s = q & 1;
-        if (tid == 0 && q + 1 < Q) issue(q + 1);
-        const bool ok = mbar_wait_bounded(&bar[s], (q >> 1) & 1, a.flag);
-        if (!ok) abort_flag = 1;
-        const int item = (int)blockIdx.x + (q / L) * (int)gridDim.x;
-        const int l = q % L;
-        const int chunk = item % nchunk;
-        const int line = (item / nchunk) % lines;
-        const int col = chunk * CX + c;
-        const bool valid = ok && col < g.nh;
-        TileSmem<CX> S{smem + s * STAGE, c};
-        float2 v[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = S.at(j + TL * m);
-
-        if (ISY) {
-            const int comp = item / (nchunk * lines);
-            line_fft<LOGN, E, (OP == OP_Y_FWD ? -1 : +1)>(v, j, S, g.t.tw);
-            if (valid) {
-                float2* out = out_ptr(a, comp) + (size_t)line * g.ny * g.nhp + col;
-#pragma unroll
-                for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * g.nhp, v[m]);
-            }
-        } else {
-            const int y = line;
-            const size_t es = (size_t)g.ny * g.nhp;
-            const size_t off = (size_t)y * g.nhp + col;
-            const float kx = col < g.nh ? __ldg(g.t.kx + col) : 0.f;
-            const float ky = __ldg(g.t.ky + y);
-            if (l == 0) {                            // operator values of this tile, kept for its loads
-#pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const float kz = __ldg(g.t.kz + j + TL * m);
-                    const float k2 = fmaf(kx, kx, fmaf(ky, ky, kz * kz));
-                    if (OP == OP_Z_ABS) lg[m] = k2 > 0.f ? log2f(k2 * g.inv_kmax2) : -INFINITY;
-                    else kap[m] = sinc_f(g.hk * sqrtf(k2)) * g.scale;
-                }
-            }
-            line_fft<LOGN, E, -1>(v, j, S, g.t.tw);
-            if (OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) {
-                // kappa (and the 1/N normalisation) is common to the three outputs
-#pragma unroll
-                for (int m = 0; m < E; ++m) v[m] = cscale(v[m], kap[m]);
-                const float2 dx = col < g.nh ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
-                const float2 dy = __ldg(g.t.dfy + y);
-#pragma unroll 1
-                for (int xi = 0; xi < 3; ++xi) {
-                    float2* out = out_ptr(a, xi);
-                    if (out == nullptr) continue;   // uniform
-                    float2 w[E];
-#pragma unroll
-                    for (int m = 0; m < E; ++m) {
-                        float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
-                        if (OP == OP_Z_GRAD_BWD) d = make_float2(-d.x, d.y);   // i k e^{-ikd/2}
-                        w[m] = cmul(v[m], d);
-                    }
-                    line_fft<LOGN, E, +1>(w, j, S, g.t.tw);
-                    if (valid) {
-#pragma unroll
-                        for (int m = 0; m < E; ++m) __stcs(out + off + (size_t)(j + TL * m) * es, w[m]);
-                    }
-                }
-            } else if (OP == OP_Z_DIV || OP == OP_Z_DIV_FWD) {
-                const int xi = l;
-                const float2 dx = col < g.nh ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
-                const float2 dy = __ldg(g.t.dfy + y);
-#pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
-                    if (OP == OP_Z_DIV) d = make_float2(-d.x, d.y);   // Eq. 4c: i k e^{-ikd/2}
-                    v[m] = cscale(cmul(v[m], d), kap[m]);            // OP_Z_DIV_FWD: Eq. 4a's operator
-                }
-                line_fft<LOGN, E, +1>(v, j, S, g.t.tw);
-                if (valid) {
-                    float2* out = out_ptr(a, xi) + off;
-#pragma unroll
-                    for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
-                }
-            } else {                                   // OP_Z_ABS
-                const int t = l == 0 ? a.load_comp[0] : a.load_comp[1];
-                const float e = g.abs_e[t], cst = g.abs_c[t] * g.scale;
-#pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const float f = lg[m] > -INFINITY ? exp2f(e * lg[m]) * cst : 0.f;   // k^{y-2} / k^{y-1}, 0 at k = 0
-                    v[m] = cscale(v[m], f);
-                }
-                line_fft<LOGN, E, +1>(v, j, S, g.t.tw);
-                if (valid) {
-                    float2* out = out_ptr(a, t) + off;
-#pragma unroll
-                    for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
-                }
-            }
-        }
-        __syncthreads();                          // stage s is free for the load of q + 2
-        if (abort_flag) {
-            if (tid == 0 && q + 1 < Q) mbar_wait_bounded(&bar[(q + 1) & 1], ((q + 1) >> 1) & 1, a.flag);
-            return;
-        }
-    }
-}
 
 // ---------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -274,7 +39,6 @@ static int encode_box(const GridC& g, float2* ptr, CUtensorMap* map) {
     return r == CUDA_SUCCESS ? 0 : -2;
 }
 
-#define KWGB_LOG_CASES(X) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 
 int make_spec_maps(const GridC& g, float2* ptr, SpecBuf* out) {
     out->p = ptr;
@@ -293,33 +57,10 @@ int make_spec_maps(const GridC& g, float2* ptr, SpecBuf* out) {
     return e;
 }
 
-template <int LOGN, int OP>
-static cudaError_t launch_t(const YZK& a, int items, cudaStream_t s) {
-    using Sh = TShape<LOGN, (OP < 2)>;
-    auto k = yz_kernel<LOGN, OP>;
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Sh::THREADS, Sh::SMEM);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
-    }
-    int grid = per_sm * a.g.num_sms;
-    if (grid > items) grid = items;
-    if (grid < 1) return cudaSuccess;
-    k<<<grid, Sh::THREADS, Sh::SMEM, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int OP>
-static cudaError_t launch_op(const YZK& a, int logn, int items, cudaStream_t s) {
-    switch (logn) {
-#define CASE(L) case L: return launch_t<L, OP>(a, items, s);
-        KWGB_LOG_CASES(CASE)
-#undef CASE
-    }
-    return cudaErrorInvalidValue;
+static cudaError_t launch_op(int op, const YZK& a, int logn, int items, cudaStream_t s) {
+    if (a.g.mixed == 2) return yz_dispatch_f16(a, op, logn, items, s);
+    if (a.g.mixed == 1) return yz_dispatch_bf16(a, op, logn, items, s);
+    return yz_dispatch_f32(a, op, logn, items, s);
 }
 
 static int chunk_count(int nh, int cx) { return (nh + cx - 1) / cx; }
@@ -347,7 +88,7 @@ cudaError_t launch_y_pass(const GridC& g, int dir, const SpecBuf* const* in, flo
     a.nloads = 1;
     a.flag = flag;
     const int items = chunk_count(g.nh, cx_of<true>(g.logny)) * g.nz * ncomp;
-    return dir < 0 ? launch_op<OP_Y_FWD>(a, g.logny, items, s) : launch_op<OP_Y_INV>(a, g.logny, items, s);
+    return launch_op(dir < 0 ? OP_Y_FWD : OP_Y_INV, a, g.logny, items, s);
 }
 
 cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, float2* const* out, int* flag,
@@ -379,11 +120,11 @@ cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, floa
     }
     const int items = chunk_count(g.nh, cx_of<false>(g.lognz)) * g.ny;
     switch (kind) {
-        case Z_GRAD_FWD: return launch_op<OP_Z_GRAD_FWD>(a, g.lognz, items, s);
-        case Z_GRAD_BWD: return launch_op<OP_Z_GRAD_BWD>(a, g.lognz, items, s);
-        case Z_DIV: return launch_op<OP_Z_DIV>(a, g.lognz, items, s);
-        case Z_DIV_FWD: return launch_op<OP_Z_DIV_FWD>(a, g.lognz, items, s);
-        case Z_ABS: return launch_op<OP_Z_ABS>(a, g.lognz, items, s);
+        case Z_GRAD_FWD: return launch_op(OP_Z_GRAD_FWD, a, g.lognz, items, s);
+        case Z_GRAD_BWD: return launch_op(OP_Z_GRAD_BWD, a, g.lognz, items, s);
+        case Z_DIV: return launch_op(OP_Z_DIV, a, g.lognz, items, s);
+        case Z_DIV_FWD: return launch_op(OP_Z_DIV_FWD, a, g.lognz, items, s);
+        case Z_ABS: return launch_op(OP_Z_ABS, a, g.lognz, items, s);
     }
     return cudaErrorInvalidValue;
 }

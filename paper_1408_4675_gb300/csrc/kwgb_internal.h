@@ -34,6 +34,7 @@ struct GridC {
     float abs_e[2];           // (y-2)/2, (y-1)/2: powers of k^2 / kmax^2 in Eq. 8
     float abs_c[2];           // kmax^(y-2), kmax^(y-1)
     int num_sms;              // SMs of the device (persistent grids)
+    int mixed;                // strided passes: 0 float32, 1 bfloat16-split, 2 float16-split tensor-core products
     Tables t;
 };
 
