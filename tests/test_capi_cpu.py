@@ -59,7 +59,10 @@ def _desc(**kw):
     (dict(pml=8, n=(16, 16, 16)), -1),   # PML leaves no interior
     (dict(y=1.0), -1),
     (dict(y=3.5), -1),
-    (dict(flags=8), -1),
+    (dict(flags=16), -1),                # unknown flag bit
+    (dict(flags=3 | 4 | 8), -1),         # both tensor-core forms
+    (dict(flags=3 | 8), 0),              # float16-split tensor-core form
+    (dict(flags=3 | 4, n=(16, 8, 16)), -7),   # tensor-core form needs ny, nz >= 16
 ])
 def test_create_validates_descriptor(lib, kw, code):
     h = ctypes.c_void_p()
