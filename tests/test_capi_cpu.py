@@ -62,7 +62,7 @@ def _desc(**kw):
     (dict(flags=16), -1),                # unknown flag bit
     (dict(flags=3 | 4 | 8), -1),         # both tensor-core forms
     (dict(flags=3 | 8), 0),              # float16-split tensor-core form
-    (dict(flags=3 | 4, n=(16, 8, 16)), -7),   # tensor-core form needs ny, nz >= 16
+    (dict(flags=3 | 4, n=(16, 8, 16), pml=2), -7),   # tensor-core form needs ny, nz >= 16
 ])
 def test_create_validates_descriptor(lib, kw, code):
     h = ctypes.c_void_p()
