@@ -237,11 +237,8 @@ static int build_tables(kwgb_sim* sim) {
     GridC& g = sim->g;
     const int64_t n[3] = {d.nx, d.ny, d.nz};
     const double dd[3] = {d.dx, d.dy, d.dz};
-    std::vector<float2> tw(1024);
-    for (int t = 0; t < 1024; ++t) {
-        const double a = 2.0 * kPi * t / 1024.0;
-        tw[t] = make_float2((float)std::cos(a), (float)-std::sin(a));
-    }
+    std::vector<float2> tw(TW_TOTAL);
+    fill_twiddle_table(tw.data());
     float2* dtw;
     if (int e = upload(sim, &dtw, tw)) return e;
     g.t.tw = dtw;

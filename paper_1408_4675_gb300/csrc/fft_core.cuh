@@ -93,6 +93,45 @@ __device__ __forceinline__ void dft_reg(float2* v) {
     }
 }
 
+// The twiddle table (Tables::tw, float2, generated in float64) has three
+// regions; every entry is exp(-2 pi i theta):
+//   [0, 1024)            theta = t / 1024
+//   stage blocks         one per (L, RP), at stw_off(L, RP): entry (r-1) L/RP + k
+//                        holds theta = k r / L for k < L/RP, 1 <= r < RP -- the
+//                        twiddles of a radix-RP Stockham pass that builds
+//                        transforms of length L.  The lanes of a warp hold
+//                        consecutive k, so they read consecutive entries (one or
+//                        two L1 wavefronts per load instead of one per line touched
+//                        by the strided index k r 1024/L).
+//   row blocks           one per M (2 <= M <= 512), at rtw_off(M): entry k holds
+//                        theta = k / (2 M), k < M (pre/post step of the real
+//                        transforms of rows of 2M values)
+__host__ __device__ constexpr int stw_off(int L, int RP) {
+    int off = 1024;
+    for (int l = 2; l < L; l *= 2)
+        for (int rp = 2; rp <= 16 && rp <= l; rp *= 2) off += l - l / rp;
+    for (int rp = 2; rp < RP; rp *= 2) off += L - L / rp;
+    return off;
+}
+__host__ __device__ constexpr int rtw_off(int M) { return stw_off(2048, 2) + M - 2; }
+constexpr int TW_TOTAL = rtw_off(1024);            // entries of the whole table
+
+// exp(DIR 2 pi i k r / L) of a radix-RP pass building length-L transforms.
+template <int DIR, int L, int RP>
+__device__ __forceinline__ float2 stage_twiddle(const float2* __restrict__ tw, int k, int r) {
+    constexpr int off = stw_off(L, RP);
+    const float2 w = __ldg(tw + off + (r - 1) * (L / RP) + k);
+    return DIR < 0 ? w : make_float2(w.x, -w.y);
+}
+
+// exp(DIR 2 pi i k / (2 M)), k < M.
+template <int DIR, int M>
+__device__ __forceinline__ float2 row_twiddle(const float2* __restrict__ tw, int k) {
+    constexpr int off = rtw_off(M);
+    const float2 w = __ldg(tw + off + k);
+    return DIR < 0 ? w : make_float2(w.x, -w.y);
+}
+
 // exp(DIR 2 pi i t / 1024) from the table tw[t] = exp(-2 pi i t / 1024).
 template <int DIR>
 __device__ __forceinline__ float2 twiddle1024(const float2* __restrict__ tw, int t) {
@@ -125,7 +164,7 @@ __device__ __forceinline__ void stockham_pass(float2 (&v)[E], int j, Smem& S,
             const int k = b & (NS - 1);
 #pragma unroll
             for (int r = 1; r < RP; ++r)
-                w[r] = cmul(w[r], twiddle1024<DIR>(tw, k * r * (1024 / (NS * RP))));
+                w[r] = cmul(w[r], stage_twiddle<DIR, NS * RP, RP>(tw, k, r));
         }
         dft_reg<RP, DIR>(w);
 #pragma unroll

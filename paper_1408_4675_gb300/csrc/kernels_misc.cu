@@ -1,9 +1,29 @@
 // Small kernels around the FFT passes: initial density, the device step
 // counter (keeps every launch of a step identical, so a step can be captured
 // in a CUDA graph once and replayed), and the sparse intensity sensors.
+#include <cmath>
+
 #include "kwgb_internal.h"
 
 namespace kwgb {
+
+// exp(-2 pi i a / b) rounded to float, a reduced modulo b first
+static float2 unit_root(long a, long b) {
+    const double t = 2.0 * 3.14159265358979323846 * (double)(a % b) / (double)b;
+    return make_float2((float)std::cos(t), (float)-std::sin(t));
+}
+
+void fill_twiddle_table(float2* out) {
+    for (int t = 0; t < 1024; ++t) out[t] = unit_root(t, 1024);
+    for (int L = 2; L <= 1024; L *= 2)
+        for (int rp = 2; rp <= 16 && rp <= L; rp *= 2) {
+            const int off = stw_off(L, rp), ns = L / rp;
+            for (int r = 1; r < rp; ++r)
+                for (int k = 0; k < ns; ++k) out[off + (r - 1) * ns + k] = unit_root((long)k * r, L);
+        }
+    for (int M = 2; M <= 512; M *= 2)
+        for (int k = 0; k < M; ++k) out[rtw_off(M) + k] = unit_root(k, 2 * M);
+}
 
 __global__ void init_rho_kernel(GridC g, Medium md, const float* __restrict__ p0, int pitch,
                                 float* rx, float* ry, float* rz) {

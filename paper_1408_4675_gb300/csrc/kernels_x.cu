@@ -15,10 +15,14 @@
 // A row of nx reals is treated as M = nx/2 complex values z[n] = x[2n] +
 // i x[2n+1]; an M-point FFT plus one post-processing step pairing bins k and
 // M-k gives the nx/2+1 bins of the real transform (and the reverse for C2R).
-// TL = M/E <= 32 threads own a row; thread j holds z[j + TL*m], i.e. the
-// float2 at x = 2(j + TL*m), so every global access of a row is coalesced.
-// A row never straddles a warp, so all synchronisation is warp-level and the
-// warps of a CTA stream their rows independently.
+// TL = M/E threads own a row; thread j holds z[j + TL*m], i.e. the float2 at
+// x = 2(j + TL*m), so every global access of a row is coalesced.  A "team"
+// is the smallest set of whole warps that holds whole rows: one warp with
+// 32/TL rows (TL <= 32), or the TL/32 warps of one row (1024-point rows:
+// E = 8, TL = 64, two warps, so that the kernels keep two CTAs per SM
+// instead of spilling 16 values per thread at one CTA).  All synchronisation
+// is within a team (a warp barrier, or a named barrier per team), so the
+// teams of a CTA stream their rows independently.
 #include "fft_core.cuh"
 #include "kwgb_internal.h"
 
@@ -26,32 +30,44 @@ namespace kwgb {
 
 constexpr int XTHREADS = 256;
 
+// Work row of a team in shared memory, and the team's barrier.
+template <int TEAM>
+struct RowSmem {
+    float2* base;
+    int bar;                                         // named barrier id (TEAM > 32)
+    __device__ __forceinline__ float2& at(int e) { return base[e + (e >> 4)]; }
+    __device__ __forceinline__ float& f(int x) { return reinterpret_cast<float*>(base)[x]; }
+    __device__ __forceinline__ void sync() {
+        if constexpr (TEAM <= 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(TEAM) : "memory");
+    }
+};
+
 template <int LOGM>
 struct XShape {
     static constexpr int M = 1 << LOGM;
-    static constexpr int E = M >= 512 ? 16 : (M >= 8 ? 8 : M);
+    static constexpr int E = M >= 8 ? 8 : M;
     static constexpr int TL = M / E;
-    static_assert(TL <= 32, "a row must fit in one warp");
-    // resident CTAs per SM the fused kernels are compiled for: 1024-wide rows
-    // (16 values per thread) get the full register file instead of spilling
-    static constexpr int MINB = LOGM >= 9 ? 1 : 2;
+    static constexpr int TEAM = TL > 32 ? TL : 32;   // threads of a team
+    static constexpr int RPT = TEAM / TL;            // rows per team
+    static constexpr int TPB = XTHREADS / TEAM;      // teams per CTA
+    static_assert(TPB >= 1 && TPB <= 15, "named barriers 1..15");
+    static constexpr int MINB = 2;                   // resident CTAs per SM the fused kernels are compiled for
     static constexpr int RPB = XTHREADS / TL;        // rows per CTA
     static constexpr int PITCH = M + M / 16 + 2;     // complex slots per row (padded, + Nyquist)
     static constexpr int SMEM = RPB * PITCH * (int)sizeof(float2);
-};
-
-struct RowSmem {
-    float2* base;
-    __device__ __forceinline__ float2& at(int e) { return base[e + (e >> 4)]; }
-    __device__ __forceinline__ float& f(int x) { return reinterpret_cast<float*>(base)[x]; }
-    __device__ __forceinline__ void sync() { __syncwarp(); }
+    using Smem = RowSmem<TEAM>;
+    // the work row of row slot r (threads r*TL .. r*TL + TL - 1) of a CTA
+    __device__ __forceinline__ static Smem row_smem(float2* smem, int r) {
+        return Smem{smem + r * PITCH, 1 + (r * TL) / TEAM};
+    }
 };
 
 // Unnormalised C2R of one row: spec[0..M] (Hermitian half spectrum) ->
 // z[m] = (x[2n], x[2n+1]) with n = j + TL*m and
 // x[i] = sum_{k<nx} X[k] exp(+2 pi i k i / nx).
 template <int LOGM>
-__device__ __forceinline__ void row_c2r(const float2* __restrict__ spec, RowSmem& S, int j,
+__device__ __forceinline__ void row_c2r(const float2* __restrict__ spec, typename XShape<LOGM>::Smem& S, int j,
                                         bool valid, const float2* __restrict__ tw,
                                         float2 (&z)[XShape<LOGM>::E]) {
     using Sh = XShape<LOGM>;
@@ -62,17 +78,17 @@ __device__ __forceinline__ void row_c2r(const float2* __restrict__ spec, RowSmem
 #pragma unroll
     for (int m = 0; m < E; ++m) t[m] = valid ? __ldcs(spec + j + TL * m) : make_float2(0.f, 0.f);
     if (valid && j == 0) nyq = __ldcs(spec + M);
-    __syncwarp();                                  // smem row free
+    S.sync();                                      // smem row free
 #pragma unroll
     for (int m = 0; m < E; ++m) S.at(j + TL * m) = t[m];
     if (j == 0) S.at(M) = nyq;
-    __syncwarp();
+    S.sync();
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = j + TL * m;
         const float2 xk = S.at(k), xm = cconj(S.at(M - k));
         const float2 a = cadd(xk, xm);
-        const float2 b = cmul(csub(xk, xm), twiddle1024<+1>(tw, k * (512 / M)));   // exp(+2 pi i k / nx)
+        const float2 b = cmul(csub(xk, xm), row_twiddle<+1, M>(tw, k));   // exp(+2 pi i k / nx)
         z[m] = make_float2(a.x - b.y, a.y + b.x);                                // a + i b
     }
     line_fft<LOGM, E, +1>(z, j, S, tw);
@@ -95,22 +111,22 @@ template <int LOGM>
 struct XStage {
     static constexpr int M = 1 << LOGM;
     static constexpr int SROW = M + 2;                   // staged complex values per row
-    static constexpr int TL = XShape<LOGM>::TL;
-    static constexpr int RPW = 32 / TL;                  // rows per warp
-    static constexpr int WARP = 2 * RPW * SROW;          // complex per warp (two stages)
+    static constexpr int RPT = XShape<LOGM>::RPT;        // rows per team
+    static constexpr int TEAM = XShape<LOGM>::TEAM;
+    static constexpr int TSTAGE = 2 * RPT * SROW;        // complex per team (two stages)
 };
 
-// Issue the copies of rows first_row .. first_row + RPW - 1 of `spec` into
-// stage buffer `dst` (RPW * SROW complex).  All 32 lanes take part.
+// Issue the copies of rows first_row .. first_row + RPT - 1 of `spec` into
+// stage buffer `dst` (RPT * SROW complex).  All threads of the team take part.
 template <int LOGM>
 __device__ __forceinline__ void stage_rows(float2* dst, const float2* __restrict__ spec, int first_row,
                                            int nrows, int nhp, int lane) {
     using St = XStage<LOGM>;
     constexpr int CH = St::SROW / 2;                     // 16-byte chunks per row
 #pragma unroll
-    for (int t = 0; t < (St::RPW * CH + 31) / 32; ++t) {
-        const int c = lane + 32 * t;
-        if (c < St::RPW * CH) {
+    for (int t = 0; t < (St::RPT * CH + St::TEAM - 1) / St::TEAM; ++t) {
+        const int c = lane + St::TEAM * t;
+        if (c < St::RPT * CH) {
             const int r = c / CH, q = c % CH;
             if (first_row + r < nrows)
                 cp_async16(dst + r * St::SROW + 2 * q, spec + (size_t)(first_row + r) * nhp + 2 * q);
@@ -121,7 +137,7 @@ __device__ __forceinline__ void stage_rows(float2* dst, const float2* __restrict
 // C2R of one row whose half spectrum X[0..M] is already in shared memory
 // (srow, unpadded): same result as row_c2r.
 template <int LOGM>
-__device__ __forceinline__ void row_c2r_staged(const float2* srow, RowSmem& S, int j,
+__device__ __forceinline__ void row_c2r_staged(const float2* srow, typename XShape<LOGM>::Smem& S, int j,
                                                const float2* __restrict__ tw,
                                                float2 (&z)[XShape<LOGM>::E]) {
     using Sh = XShape<LOGM>;
@@ -131,25 +147,25 @@ __device__ __forceinline__ void row_c2r_staged(const float2* srow, RowSmem& S, i
         const int k = j + TL * m;
         const float2 xk = srow[k], xm = cconj(srow[M - k]);
         const float2 a = cadd(xk, xm);
-        const float2 b = cmul(csub(xk, xm), twiddle1024<+1>(tw, k * (512 / M)));   // exp(+2 pi i k / nx)
+        const float2 b = cmul(csub(xk, xm), row_twiddle<+1, M>(tw, k));   // exp(+2 pi i k / nx)
         z[m] = make_float2(a.x - b.y, a.y + b.x);                                // a + i b
     }
-    __syncwarp();                                    // previous users of the work row are done
+    S.sync();                                        // previous users of the work row are done
     line_fft<LOGM, E, +1>(z, j, S, tw);
 }
 
 // Unnormalised R2C of one row: z[m] = (x[2n], x[2n+1]) -> spec[0..M].
 template <int LOGM>
-__device__ __forceinline__ void row_r2c(float2 (&z)[XShape<LOGM>::E], RowSmem& S, int j,
+__device__ __forceinline__ void row_r2c(float2 (&z)[XShape<LOGM>::E], typename XShape<LOGM>::Smem& S, int j,
                                         bool valid, const float2* __restrict__ tw,
                                         float2* __restrict__ spec) {
     using Sh = XShape<LOGM>;
     constexpr int M = Sh::M, E = Sh::E, TL = Sh::TL;
     line_fft<LOGM, E, -1>(z, j, S, tw);
-    __syncwarp();
+    S.sync();
 #pragma unroll
     for (int m = 0; m < E; ++m) S.at(j + TL * m) = z[m];
-    __syncwarp();
+    S.sync();
     if (valid) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -158,7 +174,7 @@ __device__ __forceinline__ void row_r2c(float2 (&z)[XShape<LOGM>::E], RowSmem& S
             const float2 s = cadd(zk, zm), d = csub(zk, zm);
             const float2 xe = make_float2(0.5f * s.x, 0.5f * s.y);
             const float2 xo = make_float2(0.5f * d.y, -0.5f * d.x);              // d / (2i)
-            const float2 x = cadd(xe, cmul(xo, twiddle1024<-1>(tw, k * (512 / M))));
+            const float2 x = cadd(xe, cmul(xo, row_twiddle<-1, M>(tw, k)));
             __stcs(spec + k, x);
             if (k == 0) __stcs(spec + M, csub(xe, xo));
         }
@@ -178,7 +194,7 @@ __device__ __forceinline__ float2 med2(const float* f, float s, size_t i) {
 template <int LOGM>
 __device__ __forceinline__ void finish_pressure(float2 (&p)[XShape<LOGM>::E], const GridC& g,
                                                 const SensorC& sens, const StepC& st,
-                                                RowSmem& S, int j, bool valid, int row,
+                                                typename XShape<LOGM>::Smem& S, int j, bool valid, int row,
                                                 float2* __restrict__ P) {
     using Sh = XShape<LOGM>;
     constexpr int E = Sh::E, TL = Sh::TL;
@@ -206,14 +222,14 @@ __device__ __forceinline__ void finish_pressure(float2 (&p)[XShape<LOGM>::E], co
         }
     }
     if (sens.row_ptr) {                               // uniform over the launch
-        __syncwarp();
+        S.sync();
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int x = 2 * (j + TL * m);
             S.f(x) = p[m].x;
             S.f(x + 1) = p[m].y;
         }
-        __syncwarp();
+        S.sync();
         if (valid) {
             const int e0 = __ldg(sens.row_ptr + row), e1 = __ldg(sens.row_ptr + row + 1);
             for (int e = e0 + j; e < e1; e += TL) {
@@ -240,10 +256,11 @@ __device__ __forceinline__ float2* pick3w(float2* const (&p)[3], int i) {
     return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);
 }
 
-// The fused x kernels are persistent: warp w of the grid handles row groups
-// w, w + W, w + 2W, ... (a group is the 32/TL rows one warp transforms at
-// once), and walks the components of each group as a sequence of items; the
-// spectrum rows of item i+1 are staged while item i is processed.
+// x_dens is persistent: team w of the grid handles row groups w, w + W,
+// w + 2W, ... (a group is the rows one team transforms at once), and walks
+// the components of each group as a sequence of items; the spectrum rows of
+// item i+1 are staged while item i is processed.  x_vel and x_eos take one
+// row per TL threads per launch slot.
 struct XVelK {
     GridC g;
     Medium md;
@@ -262,7 +279,7 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_vel_kernel(con
     const bool valid = row < nrows;
     const int rr = valid ? row : 0;
     const int y = rr % g.ny, z = rr / g.ny;
-    RowSmem S{smem + r * Sh::PITCH};
+    typename Sh::Smem S = Sh::row_smem(smem, r);
     const size_t rb = (size_t)rr * g.nx;
     const float* rho0 = K.md.rho0;
     const float rho0s = K.md.rho0_s;
@@ -331,17 +348,17 @@ template <int LOGM, bool FUSED_EOS>
 __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(const XDensK K) {
     using Sh = XShape<LOGM>;
     using St = XStage<LOGM>;
-    constexpr int E = Sh::E, TL = Sh::TL, RPW = St::RPW, WPB = XTHREADS / 32;
+    constexpr int E = Sh::E, TL = Sh::TL, RPW = Sh::RPT, TPB = Sh::TPB;
     extern __shared__ __align__(16) float2 smem[];
     const GridC& g = K.g;
     const Medium& md = K.md;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int team = threadIdx.x / Sh::TEAM, lane = threadIdx.x % Sh::TEAM;
     const int r = lane / TL, j = lane % TL;
-    RowSmem S{smem + (warp * RPW + r) * Sh::PITCH};
-    float2* stage = smem + Sh::RPB * Sh::PITCH + warp * St::WARP;
+    typename Sh::Smem S = Sh::row_smem(smem, team * RPW + r);
+    float2* stage = smem + Sh::RPB * Sh::PITCH + team * St::TSTAGE;
     const int nrows = g.ny * g.nz;
     const int ngroups = (nrows + RPW - 1) / RPW;
-    const int gw = blockIdx.x * WPB + warp, nw = gridDim.x * WPB;
+    const int gw = blockIdx.x * TPB + team, nw = gridDim.x * TPB;
     const int mygroups = gw < ngroups ? (ngroups - 1 - gw) / nw + 1 : 0;
 
     if (mygroups > 0) stage_rows<LOGM>(stage, K.a.D[0], gw * RPW, nrows, g.nhp, lane);
@@ -364,7 +381,7 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
 #pragma unroll 1
         for (int xi = 0; xi < 3; ++xi) {
             const int it = 3 * gi + xi;
-            __syncwarp();
+            S.sync();
             if (xi < 2) stage_rows<LOGM>(stage + ((it + 1) & 1) * RPW * St::SROW, pick3(K.a.D, xi + 1), grp * RPW,
                                          nrows, g.nhp, lane);
             else if (gi + 1 < mygroups)
@@ -379,7 +396,7 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
                 r0[m] = med2(md.rho0, md.rho0_s, rb + 2 * (j + TL * m));
             }
             cp_async_wait1();
-            __syncwarp();
+            S.sync();
             float2 d[E];
             row_c2r_staged<LOGM>(stage + (it & 1) * RPW * St::SROW + r * St::SROW, S, j, g.t.tw, d);
 #pragma unroll
@@ -406,11 +423,11 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
             const int p0 = valid ? __ldg(K.src.row_ptr + rr) : 0;
             const int p1 = valid ? __ldg(K.src.row_ptr + rr + 1) : 0;
             const int64_t n = *K.st.step;
-            __syncwarp();
+            S.sync();
             if (p1 > p0) {
                 for (int x = j; x < g.nx; x += TL) S.f(x) = 0.f;
             }
-            __syncwarp();
+            S.sync();
             for (int p = p0 + j; p < p1; p += TL) {
                 const int c0 = __ldg(K.src.pt_c + p), c1 = __ldg(K.src.pt_c + p + 1);
                 float acc = 0.f;
@@ -422,7 +439,7 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
                 const float c = md.c0 ? __ldg(md.c0 + rb + x) : md.c0_s;
                 S.f(x) = __fdividef(acc, c);           // dt * 2 s / (3 c0 dx)
             }
-            __syncwarp();
+            S.sync();
             if (p1 > p0) {
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
@@ -490,7 +507,7 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_eos_kernel(con
     const int row = blockIdx.x * Sh::RPB + r;
     const bool valid = row < nrows;
     const int rr = valid ? row : 0;
-    RowSmem S{smem + r * Sh::PITCH};
+    typename Sh::Smem S = Sh::row_smem(smem, r);
     const size_t rb = (size_t)rr * g.nx;
     // Eq. 6 with Eq. 8 and Eq. 3:
     //   p = c0^2 (rho + B/2A rho^2/rho0) + c0^2 tau a1 - c0^2 eta a2,
@@ -552,7 +569,7 @@ __global__ void __launch_bounds__(XTHREADS) x_r2c_kernel(const XPlainK K) {
     const int row = blockIdx.x * Sh::RPB + r;
     const bool valid = row < K.g.ny * K.g.nz;
     const int rr = valid ? row : 0;
-    RowSmem S{smem + r * Sh::PITCH};
+    typename Sh::Smem S = Sh::row_smem(smem, r);
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m)
@@ -569,7 +586,7 @@ __global__ void __launch_bounds__(XTHREADS) x_c2r_kernel(const XPlainK K) {
     const int row = blockIdx.x * Sh::RPB + r;
     const bool valid = row < K.g.ny * K.g.nz;
     const int rr = valid ? row : 0;
-    RowSmem S{smem + r * Sh::PITCH};
+    typename Sh::Smem S = Sh::row_smem(smem, r);
     float2 v[E];
     row_c2r<LOGM>(K.cin + (size_t)rr * K.g.nhp, S, j, valid, K.g.t.tw, v);
     if (valid) {
@@ -596,7 +613,7 @@ template <int LOGM, class Kern, class Args>
 static cudaError_t launch_persistent(Kern k, const GridC& g, const Args& args, cudaStream_t s) {
     using Sh = XShape<LOGM>;
     using St = XStage<LOGM>;
-    const int smem_bytes = (Sh::RPB * Sh::PITCH + (XTHREADS / 32) * St::WARP) * (int)sizeof(float2);
+    const int smem_bytes = (Sh::RPB * Sh::PITCH + Sh::TPB * St::TSTAGE) * (int)sizeof(float2);
     int per_sm = 0;
     if (smem_bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
@@ -605,8 +622,8 @@ static cudaError_t launch_persistent(Kern k, const GridC& g, const Args& args, c
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, XTHREADS, smem_bytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const int ngroups = (g.ny * g.nz + St::RPW - 1) / St::RPW;
-    int blocks = (ngroups + XTHREADS / 32 - 1) / (XTHREADS / 32);
+    const int ngroups = (g.ny * g.nz + Sh::RPT - 1) / Sh::RPT;
+    int blocks = (ngroups + Sh::TPB - 1) / Sh::TPB;
     if (blocks > per_sm * g.num_sms) blocks = per_sm * g.num_sms;
     k<<<blocks, XTHREADS, smem_bytes, s>>>(args);
     return cudaGetLastError();

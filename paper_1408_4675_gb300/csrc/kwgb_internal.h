@@ -7,11 +7,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fft_core.cuh"
+
 namespace kwgb {
+
+// Fill the TW_TOTAL-entry twiddle table (layout in fft_core.cuh) in float64.
+void fill_twiddle_table(float2* out);
 
 // 1-D tables in device memory (generated on the host in float64, stored as float).
 struct Tables {
-    const float2* tw;         // exp(-2 pi i t / 1024), t < 1024 (FFT twiddles)
+    const float2* tw;         // FFT twiddles, TW_TOTAL entries (regions: fft_core.cuh)
     const float* kx;          // Eq. 5 wavenumbers: kx for the half spectrum (nh values)
     const float* ky;          //   ky (ny), kz (nz), FFT storage order
     const float* kz;

@@ -32,8 +32,8 @@ constexpr int kMaxNhp = ((kMaxN / 2 + 1) + 15) / 16 * 16;          // padded spe
 constexpr size_t kSpec = (size_t)kMaxNhp * kMaxN * kMaxN;          // complex per spectrum
 // layout of the scratch array, in float2 units (every block 256-byte aligned)
 constexpr size_t kOffSpec = 0;                                     // 3 spectra
-constexpr size_t kOffTw = 3 * kSpec;                               // 1024 twiddles
-constexpr size_t kOffK = kOffTw + 1024;                            // kx, ky, kz (float)
+constexpr size_t kOffTw = 3 * kSpec;                               // TW_TOTAL twiddles
+constexpr size_t kOffK = kOffTw + (TW_TOTAL + 31) / 32 * 32;       // kx, ky, kz (float)
 constexpr size_t kOffDf = kOffK + 128;                             // dfx, dfy, dfz (kx.. take 256 floats)
 constexpr size_t kOffFlag = kOffDf + 256;                          // device status word
 constexpr size_t kTotal = kOffFlag + 32;
@@ -131,10 +131,12 @@ extern "C" int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const fl
     g.num_sms = sms;
 
     // tables, built here in float64 and copied into the scratch (fixed-size host arrays)
-    float2 tw[1024];
-    for (int t = 0; t < 1024; ++t) {
-        const double a = 2.0 * kPi * t / 1024.0;
-        tw[t] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    static float2 tw[TW_TOTAL];                 // constant; filled once under the setup lock
+    {
+        std::lock_guard<std::mutex> lk(g_setup_mu);
+        static bool filled = false;
+        if (!filled) fill_twiddle_table(tw);
+        filled = true;
     }
     float kt[256];
     float2 df[256];
