@@ -146,7 +146,8 @@ __device__ __forceinline__ float2 twiddle1024(const float2* __restrict__ tw, int
 // takes an RP-point DFT and sends output q to element
 // (b / NS) * NS * RP + (b mod NS) + q * NS.
 // LAST: that position is the thread's own register layout; otherwise the
-// outputs go through shared memory (S(e) gives element e's slot).
+// outputs go through shared memory (S.at(e) gives element e's slot; an Smem
+// with PINGPONG has two buffers, S.at_pp<B>(e)).
 template <int LOGN, int E, int RP, int NS, int DIR, bool LAST, class Smem>
 __device__ __forceinline__ void stockham_pass(float2 (&v)[E], int j, Smem& S,
                                               const float2* __restrict__ tw) {
@@ -175,6 +176,29 @@ __device__ __forceinline__ void stockham_pass(float2 (&v)[E], int j, Smem& S,
         // i.e. register i + q*NB of this thread.
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = o[m];
+    } else if constexpr (Smem::PINGPONG) {
+        // Two exchange buffers, chosen at compile time: exchange p (0-based,
+        // this pass's index; all passes before the last have radix E) writes
+        // the scratch buffer for even p and the arrived tile for odd p.  The
+        // buffer written was last read before the previous exchange's barrier
+        // (or, for p = 0, before the previous transform's second-last
+        // barrier), so one barrier per exchange suffices -- except when a
+        // transform has an odd number of exchanges: then its last exchange
+        // and the next transform's first both write the scratch buffer.
+        constexpr int P = ilog2c(NS) / ilog2c(E);
+        constexpr int NX = (LOGN + ilog2c(E) - 1) / ilog2c(E) - 1;
+        constexpr int B = (P & 1) ? 0 : 1;
+        if constexpr (P == 0 && (NX & 1)) S.sync();
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int b = j + TL * i;
+            const int base = (b / NS) * NS * RP + (b & (NS - 1));
+#pragma unroll
+            for (int q = 0; q < RP; ++q) S.template at_pp<B>(base + q * NS) = o[i + q * NB];
+        }
+        S.sync();
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = S.template at_pp<B>(j + TL * m);
     } else {
         S.sync();
 #pragma unroll

@@ -35,6 +35,7 @@ template <int TEAM>
 struct RowSmem {
     float2* base;
     int bar;                                         // named barrier id (TEAM > 32)
+    static constexpr bool PINGPONG = false;
     __device__ __forceinline__ float2& at(int e) { return base[e + (e >> 4)]; }
     __device__ __forceinline__ float& f(int x) { return reinterpret_cast<float*>(base)[x]; }
     __device__ __forceinline__ void sync() {
@@ -106,6 +107,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int LOGM>
 struct XStage {
@@ -495,26 +497,34 @@ struct XEosK {
     XEosArgs a;
 };
 
+// The two absorption spectra rows are copied into shared memory (cp.async)
+// first, so that their loads overlap the medium loads and the local part.
 template <int LOGM>
 __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_eos_kernel(const XEosK K) {
     using Sh = XShape<LOGM>;
+    using St = XStage<LOGM>;
     constexpr int E = Sh::E, TL = Sh::TL;
-    extern __shared__ float2 smem[];
+    constexpr int BUF = Sh::RPT * St::SROW;            // one spectrum's rows of a team
+    extern __shared__ __align__(16) float2 smem[];
     const GridC& g = K.g;
     const Medium& md = K.md;
     const int r = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int team = threadIdx.x / Sh::TEAM, lane = threadIdx.x % Sh::TEAM;
     const int nrows = g.ny * g.nz;
     const int row = blockIdx.x * Sh::RPB + r;
     const bool valid = row < nrows;
     const int rr = valid ? row : 0;
     typename Sh::Smem S = Sh::row_smem(smem, r);
+    float2* stage = smem + Sh::RPB * Sh::PITCH + team * 2 * BUF;
+    const int first = blockIdx.x * Sh::RPB + team * Sh::RPT;
+    stage_rows<LOGM>(stage, K.a.A1, first, nrows, g.nhp, lane);
+    stage_rows<LOGM>(stage + BUF, K.a.A2, first, nrows, g.nhp, lane);
+    cp_async_commit();
     const size_t rb = (size_t)rr * g.nx;
     // Eq. 6 with Eq. 8 and Eq. 3:
     //   p = c0^2 (rho + B/2A rho^2/rho0) + c0^2 tau a1 - c0^2 eta a2,
     //   a1 = IFT{k^{y-2} FT{rho0 sum d}}, a2 = IFT{k^{y-1} FT{rho}},
     //   tau = -2 alpha0 c0^{y-1}, eta = 2 alpha0 c0^y tan(pi y / 2).
-    // The local part and the two coefficients are formed before the two
-    // row transforms so that the field loads overlap them.
     float2 p0[E], ct[E], ce[E];
     const float ym1 = md.y - 1.0f;
 #pragma unroll
@@ -538,12 +548,15 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_eos_kernel(con
         ce[m] = make_float2(-cx2 * 2.0f * al.x * px * c.x * md.tan_pi_y_2,
                             -cy2 * 2.0f * al.y * py * c.y * md.tan_pi_y_2);                        // -c0^2 eta
     }
+    cp_async_wait0();
+    S.sync();
+    const float2* cur = stage + (r % Sh::RPT) * St::SROW;
     float2 a[E];
-    row_c2r<LOGM>(K.a.A1 + (size_t)rr * g.nhp, S, j, valid, g.t.tw, a);
+    row_c2r_staged<LOGM>(cur, S, j, g.t.tw, a);
 #pragma unroll
     for (int m = 0; m < E; ++m)
         p0[m] = make_float2(fmaf(ct[m].x, a[m].x, p0[m].x), fmaf(ct[m].y, a[m].y, p0[m].y));
-    row_c2r<LOGM>(K.a.A2 + (size_t)rr * g.nhp, S, j, valid, g.t.tw, a);
+    row_c2r_staged<LOGM>(cur + BUF, S, j, g.t.tw, a);
 #pragma unroll
     for (int m = 0; m < E; ++m)
         p0[m] = make_float2(fmaf(ce[m].x, a[m].x, p0[m].x), fmaf(ce[m].y, a[m].y, p0[m].y));
@@ -667,7 +680,7 @@ cudaError_t launch_x_eos(const GridC& g, const Medium& m, const SensorC& sens,
     XEosK K{g, m, sens, st, a};
     switch (g.lognx - 1) {
 #define CASE(L) \
-    case L: return launch_rows(x_eos_kernel<L>, XShape<L>::RPB, XShape<L>::SMEM, g, K, s);
+    case L: return launch_rows(x_eos_kernel<L>, XShape<L>::RPB, XShape<L>::SMEM + XShape<L>::TPB * XStage<L>::TSTAGE * (int)sizeof(float2), g, K, s);
         KWGB_LOGM_CASES(CASE)
 #undef CASE
     }

@@ -29,11 +29,23 @@ namespace kwgb {
 enum { OP_Y_FWD = 0, OP_Y_INV = 1, OP_Z_GRAD_FWD = 2, OP_Z_GRAD_BWD = 3, OP_Z_DIV = 4, OP_Z_ABS = 5,
        OP_Z_DIV_FWD = 6 };
 
-template <int CX>
+// Column c of a tile in shared memory.  The TMA lands element e of every
+// column as row e (CX float2, dense): raw(e).  The float32 passes (PP)
+// exchange through two buffers, the arrived tile (B = 0) and a scratch tile
+// (B = 1), one barrier per exchange (fft_core.cuh), and swizzle 64-byte rows
+// (CX = 8) as row e ^ ((e >> 3) & 1), so that the first pass, whose warps
+// write rows 8b + q for consecutive b, spreads them over both bank halves.
+template <int CX, bool PP>
 struct TileSmem {
-    float2* buf;
+    float2* buf;              // the arrived tile
+    float2* scr;              // scratch tile (PP)
     int c;
+    static constexpr bool PINGPONG = PP;
+    __device__ __forceinline__ static int row(int e) { return e; }
     __device__ __forceinline__ float2& at(int e) { return buf[e * CX + c]; }
+    __device__ __forceinline__ float2& raw(int e) { return buf[e * CX + c]; }
+    template <int B>
+    __device__ __forceinline__ float2& at_pp(int e) { return (B ? scr : buf)[row(e) * CX + c]; }
     __device__ __forceinline__ void sync() { __syncthreads(); }
 };
 
@@ -50,7 +62,8 @@ struct TShape {
     static constexpr int BOX = N < 256 ? N : 256;
     static constexpr int NBOX = N / BOX;
     static constexpr int STAGE = N * CX;                       // complex elements per stage
-    static constexpr int SMEM = 2 * STAGE * (int)sizeof(float2) + 64;
+    // two TMA stages, plus the scratch exchange buffer of the float32 passes
+    static constexpr int smem(int mixed) { return (mixed ? 2 : 3) * STAGE * (int)sizeof(float2) + 64; }
 };
 
 struct alignas(64) YZK {
@@ -90,7 +103,7 @@ __device__ __forceinline__ float2* out_ptr(const YZK& a, int i) {
 // Inverse transform of the register layout v (element j + TL*m of column c):
 // float32 register passes, or (MIXED) through the tile in shared memory.
 template <int LOGN, int E, int CX, int THREADS, int MIXED>
-__device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX>& S, float2* tile,
+__device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX, MIXED == 0>& S, float2* tile,
                                              const float2* __restrict__ tw, float* colscale) {
     constexpr int TL = (1 << LOGN) / E;
     if constexpr (MIXED == 0) {
@@ -118,7 +131,8 @@ yz_kernel(const __grid_constant__ YZK a) {
     extern __shared__ __align__(128) float2 smem[];
     __shared__ int abort_flag;
     __shared__ float colscale[16];                  // per-column scales of the float16-split form
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
+    float2* scratch = smem + 2 * STAGE;             // float32 exchanges (not used by MIXED)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (MIXED ? 2 : 3) * STAGE);
     const GridC& g = a.g;
     const int tid = threadIdx.x;
     const int c = tid % CX, j = tid / CX;
@@ -175,13 +189,13 @@ yz_kernel(const __grid_constant__ YZK a) {
         const int line = (item / nchunk) % lines;
         const int col = chunk * CX + c;
         const bool valid = ok && col < g.nh;
-        TileSmem<CX> S{smem + s * STAGE, c};
+        TileSmem<CX, MIXED == 0> S{smem + s * STAGE, scratch, c};
         constexpr int THREADS = Sh::THREADS;
         float2 v[E];
         if constexpr (MIXED != 0)
             tile_fft_tc<LOGN, CX, (ISY ? (OP == OP_Y_FWD ? -1 : +1) : -1), THREADS, MIXED>(smem + s * STAGE, g.t.tw, colscale);
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = S.at(j + TL * m);
+        for (int m = 0; m < E; ++m) v[m] = S.raw(j + TL * m);
 
         if (ISY) {
             const int comp = item / (nchunk * lines);
@@ -277,16 +291,16 @@ inline cudaError_t launch_t(const YZK& a, int items, cudaStream_t s) {
     auto k = yz_kernel<LOGN, OP, MIXED>;
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::smem(MIXED));
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Sh::THREADS, Sh::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Sh::THREADS, Sh::smem(MIXED));
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
     int grid = per_sm * a.g.num_sms;
     if (grid > items) grid = items;
     if (grid < 1) return cudaSuccess;
-    k<<<grid, Sh::THREADS, Sh::SMEM, s>>>(a);
+    k<<<grid, Sh::THREADS, Sh::smem(MIXED), s>>>(a);
     return cudaGetLastError();
 }
 
