@@ -222,26 +222,44 @@ yz_kernel(const __grid_constant__ YZK a) {
             }
             if (!MIXED) line_fft<LOGN, E, -1>(v, j, S, g.t.tw);
             if (OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) {
-                // kappa (and the 1/N normalisation) is common to the three outputs
+                // kappa (and the 1/N normalisation) is common to the three outputs.
+                // The x and y shift operators do not vary along z, so they commute
+                // with the inverse z transform: outputs 0 and 1 are dx Q and dy Q
+                // with Q = IFT_z{kappa P}, and only output 2 needs a second inverse
+                // transform, of kappa dz P.
+                float2 dx = col < g.nh ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
+                float2 dy = __ldg(g.t.dfy + y);
+                if (OP == OP_Z_GRAD_BWD) {                       // i k e^{-ikd/2}
+                    dx = make_float2(-dx.x, dx.y);
+                    dy = make_float2(-dy.x, dy.y);
+                }
+                float2 w[E];
 #pragma unroll
-                for (int m = 0; m < E; ++m) v[m] = cscale(v[m], kap[m]);
-                const float2 dx = col < g.nh ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
-                const float2 dy = __ldg(g.t.dfy + y);
-#pragma unroll 1
-                for (int xi = 0; xi < 3; ++xi) {
-                    float2* out = out_ptr(a, xi);
-                    if (out == nullptr) continue;   // uniform
-                    float2 w[E];
+                for (int m = 0; m < E; ++m) {
+                    v[m] = cscale(v[m], kap[m]);
+                    float2 d = __ldg(g.t.dfz + j + TL * m);
+                    if (OP == OP_Z_GRAD_BWD) d = make_float2(-d.x, d.y);
+                    w[m] = cmul(v[m], d);
+                }
+                float2* o0 = a.out[0];
+                float2* o1 = a.out[1];
+                float2* o2 = a.out[2];
+                if (o0 != nullptr || o1 != nullptr) {           // uniform
+                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, colscale);
+                    if (valid) {
 #pragma unroll
-                    for (int m = 0; m < E; ++m) {
-                        float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
-                        if (OP == OP_Z_GRAD_BWD) d = make_float2(-d.x, d.y);   // i k e^{-ikd/2}
-                        w[m] = cmul(v[m], d);
+                        for (int m = 0; m < E; ++m) {
+                            const size_t o = off + (size_t)(j + TL * m) * es;
+                            if (o0 != nullptr) __stcs(o0 + o, cmul(v[m], dx));
+                            if (o1 != nullptr) __stcs(o1 + o, cmul(v[m], dy));
+                        }
                     }
+                }
+                if (o2 != nullptr) {
                     inverse_tile<LOGN, E, CX, THREADS, MIXED>(w, j, S, smem + s * STAGE, g.t.tw, colscale);
                     if (valid) {
 #pragma unroll
-                        for (int m = 0; m < E; ++m) __stcs(out + off + (size_t)(j + TL * m) * es, w[m]);
+                        for (int m = 0; m < E; ++m) __stcs(o2 + off + (size_t)(j + TL * m) * es, w[m]);
                     }
                 }
             } else if (OP == OP_Z_DIV || OP == OP_Z_DIV_FWD) {
