@@ -309,6 +309,8 @@ def run_ours(args):
         out["mixed_bf16"] = step_variant(args, kwgb, torch, 3, 4)
         out["also_1024"] = step_variant(args, kwgb, torch, 4, 0)
         out["adjoint"] = adjoint_measure(kwgb, torch)
+    if not args.no_extra and world == 1:
+        out["cufft_unfused"] = cufft_unfused(args, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
         s, cores = oracle_sample(args.config, 128, 6)
         cpu_ms = 1e3 * s * scale_to(128, cfg["shape"][0])
@@ -374,6 +376,165 @@ def adjoint_measure(kwgb, torch):
             "forward_ms_per_step": round(fwd, 4), "forward_plus_adjoint_ms_per_step": round(tot, 4),
             "device_gb": round(prob.last_device_bytes / 1e9, 3), "J": J,
             "grad_norm_phases": float(np.linalg.norm(dphi))}
+
+
+class CufftStep:
+    """Comparator timed beside the library, not part of it: the same workload
+    stepped by plain PyTorch ops -- 14 cuFFT 3-D real transforms per step
+    (torch.fft.rfftn / irfftn), stored 3-D operator arrays (i k kappa
+    exp(+-i k d/2) per axis, k^{y-2}, k^{y-1}) and one unfused kernel per
+    element-wise operation: the direct GPU transcription of Eqs. 4a-4d, 6 and
+    8 (readings as in the library: PML, staggered rho0, additive mass source,
+    initial pressure).  Sensors: p_max and sum p^2 at each mask."""
+
+    def __init__(self, cfg, device="cuda"):
+        import torch
+        self.t = torch
+        self.dev = device
+        nz, ny, nx = self.shape = tuple(cfg["shape"])
+        self.dt = dt = float(cfg["dt"])
+        y = float(cfg["alpha_power"])
+        self.nonlinear = bool(cfg["flags"] & 1)
+        self.absorbing = bool(cfg["flags"] & 2)
+        f64 = dict(dtype=torch.float64, device=device)
+
+        def field(v):
+            a = torch.as_tensor(np.asarray(v, dtype=np.float32), device=device)
+            return a.expand(nz, ny, nx).contiguous() if a.ndim == 0 else a.reshape(nz, ny, nx)
+
+        self.c0, self.rho0, self.bona, self.alpha0 = (field(cfg[k]) for k in ("c0", "rho0", "bona", "alpha0"))
+
+        def kvec(n, d, half=False):
+            m = torch.arange(n // 2 + 1 if half else n, **f64)
+            if not half:
+                m = torch.where(m < n // 2, m, m - n)            # Eq. 5, Nyquist at -N/2
+            return m * (2.0 * math.pi / (d * n))
+
+        dx, dy, dz = cfg["d"]
+        kx = kvec(nx, dx, True).reshape(1, 1, -1)
+        ky = kvec(ny, dy).reshape(1, -1, 1)
+        kz = kvec(nz, dz).reshape(-1, 1, 1)
+        kmag = torch.sqrt(kx * kx + ky * ky + kz * kz)
+        arg = float(cfg["c_ref"]) * kmag * dt / 2.0
+        kappa = torch.where(arg > 0, torch.sin(arg) / torch.where(arg > 0, arg, 1.0), 1.0)
+        self.Dp, self.Dm = [], []
+        for k, d in ((kx, dx), (ky, dy), (kz, dz)):
+            for sign, lst in ((1.0, self.Dp), (-1.0, self.Dm)):
+                op = (1j * k) * torch.exp(sign * 1j * k * d / 2.0) * kappa
+                lst.append(op.to(torch.complex64))
+        if self.absorbing:
+            safe = torch.where(kmag > 0, kmag, 1.0)
+            self.tau_op = torch.where(kmag > 0, safe ** (y - 2.0), 0.0).float()
+            self.eta_op = torch.where(kmag > 0, safe ** (y - 1.0), 0.0).float()
+            c64, a64 = self.c0.double(), self.alpha0.double()
+            self.tau = (-2.0 * a64 * c64 ** (y - 1.0)).float()
+            self.eta = (2.0 * a64 * c64 ** y * math.tan(math.pi * y / 2.0)).float()
+        del kmag, arg, kappa
+        self.rho0_sg = [0.5 * (self.rho0 + torch.roll(self.rho0, -1, dims=a)) for a in (2, 1, 0)]
+
+        def pml(n, size, alpha, d, stag):
+            s = torch.arange(n, **f64) + (0.5 if stag else 0.0)
+            if size <= 0:
+                return torch.ones(n, **f64)
+            depth = torch.clamp(torch.maximum(size - s, s - (n - 1 - size)), min=0.0)
+            return torch.exp(-alpha * (float(cfg["c_ref"]) / d) * (depth / size) ** 4 * dt / 2.0)
+
+        shp = [(1, 1, nx), (1, ny, 1), (nz, 1, 1)]
+        ns, ds = (nx, ny, nz), (dx, dy, dz)
+        self.f = [pml(ns[a], cfg["pml_size"][a], cfg["pml_alpha"][a], ds[a], False).float().reshape(shp[a])
+                  for a in range(3)]
+        self.fs = [pml(ns[a], cfg["pml_size"][a], cfg["pml_alpha"][a], ds[a], True).float().reshape(shp[a])
+                   for a in range(3)]
+        zeros = lambda: torch.zeros(self.shape, dtype=torch.float32, device=device)
+        self.u = [zeros() for _ in range(3)]
+        self.rho = [zeros() for _ in range(3)]
+        self.p = zeros()
+        if cfg.get("p0") is not None:
+            p0 = field(cfg["p0"])
+            self.p = p0.clone()
+            self.rho = [p0 / (3.0 * self.c0 ** 2) for _ in range(3)]
+            P = self.rfft(p0)
+            self.u = [dt / (2.0 * self.rho0_sg[i]) * self.irfft(P * self.Dp[i]) for i in range(3)]
+        c0f = self.c0.reshape(-1)
+        self.src = []
+        for idx, sig in cfg["sources"]:
+            ii = torch.as_tensor(np.asarray(idx, dtype=np.int64), device=device)
+            sg = torch.as_tensor(np.atleast_2d(np.asarray(sig, dtype=np.float32)), device=device)
+            scale = dt * 2.0 / (3.0 * c0f[ii] * dx)
+            self.src.append((ii, sg, scale))
+        self.sens = []
+        for idx, _ in cfg["sensors"]:
+            n = nz * ny * nx if idx is None else len(idx)
+            ii = None if idx is None else torch.as_tensor(np.asarray(idx, dtype=np.int64), device=device)
+            self.sens.append((ii, torch.full((n,), -math.inf, device=device),
+                              torch.zeros(n, dtype=torch.float64, device=device)))
+        self.n = 0
+
+    def rfft(self, a):
+        return self.t.fft.rfftn(a, dim=(0, 1, 2))
+
+    def irfft(self, a):
+        return self.t.fft.irfftn(a, s=self.shape, dim=(0, 1, 2))
+
+    def step(self, nsteps=1):
+        t, dt = self.t, self.dt
+        for _ in range(nsteps):
+            P = self.rfft(self.p)                                                    # 1 FFT
+            for i in range(3):
+                g = self.irfft(P * self.Dp[i])                                       # Eq. 4a
+                self.u[i] = self.fs[i] * (self.fs[i] * self.u[i] - dt * g / self.rho0_sg[i])   # Eq. 4b
+            d = [self.irfft(self.rfft(self.u[i]) * self.Dm[i]) for i in range(3)]    # Eq. 4c
+            for i in range(3):
+                num = self.f[i] * (self.f[i] * self.rho[i] - dt * self.rho0 * d[i])
+                self.rho[i] = num / (1.0 + 2.0 * dt * d[i]) if self.nonlinear else num      # Eq. 4d
+            for ii, sg, scale in self.src:
+                if self.n < sg.shape[-1]:
+                    s = sg[:, self.n] if sg.shape[0] > 1 else sg[0, self.n]
+                    add = scale * s
+                    for i in range(3):
+                        self.rho[i].view(-1).index_add_(0, ii, add)
+            rho = self.rho[0] + self.rho[1] + self.rho[2]
+            q = rho + (self.bona / 2.0) * rho * rho / self.rho0 if self.nonlinear else rho
+            if self.absorbing:
+                dsum = self.rho0 * (d[0] + d[1] + d[2])
+                Ld = (-self.tau * self.irfft(self.tau_op * self.rfft(dsum))
+                      + self.eta * self.irfft(self.eta_op * self.rfft(rho)))       # Eq. 8
+                q = q - Ld
+            self.p = self.c0 * self.c0 * q                                           # Eq. 6
+            self.n += 1
+            pf = self.p.reshape(-1)
+            for ii, pm, p2 in self.sens:
+                v = pf if ii is None else pf[ii]
+                t.maximum(pm, v, out=pm)
+                p2.add_(v.double() * v.double())
+
+
+def cufft_unfused(args, torch):
+    """Time CufftStep on the bench workload: ms per step with CUDA events."""
+    cfg = inputs.make_config(args.config, n=args.n, n_steps=args.warmup + args.steps + 8)
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
+    try:
+        st = CufftStep(cfg)
+    except torch.cuda.OutOfMemoryError as e:
+        return {"unavailable": "out of memory: %s" % str(e).splitlines()[0]}
+    stream = torch.cuda.current_stream()
+    st.step(args.warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    peak_gb = torch.cuda.max_memory_allocated() / 1e9
+    del st
+    torch.cuda.empty_cache()
+    return {"ms_per_step": round(ms, 3), "ffts_per_step": 14,
+            "what": "same workload stepped by plain PyTorch CUDA ops: cuFFT 3-D R2C/C2R transforms, stored "
+                    "3-D operator arrays, unfused element-wise kernels (comparator, not the library)",
+            "peak_device_gb": round(peak_gb, 2)}
 
 
 def e2e(args, cfg, kwgb, torch):

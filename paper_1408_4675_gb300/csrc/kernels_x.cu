@@ -497,14 +497,41 @@ struct XEosK {
     XEosArgs a;
 };
 
-// The two absorption spectra rows are copied into shared memory (cp.async)
-// first, so that their loads overlap the medium loads and the local part.
+// Copy rows first_row .. first_row + RPT - 1 of a real field (nx = 2M floats
+// per row, row pitch `pitch` floats) into dst (M float2 per row).
+template <int LOGM>
+__device__ __forceinline__ void stage_real_rows(float2* dst, const float* __restrict__ src, size_t pitch,
+                                                int first_row, int nrows, int lane) {
+    using Sh = XShape<LOGM>;
+    constexpr int CH = Sh::M / 2;                        // 16-byte chunks per row
+#pragma unroll
+    for (int t = 0; t < (Sh::RPT * CH + Sh::TEAM - 1) / Sh::TEAM; ++t) {
+        const int c = lane + Sh::TEAM * t;
+        if (c < Sh::RPT * CH) {
+            const int r = c / CH, q = c % CH;
+            if (first_row + r < nrows) cp_async16(dst + r * Sh::M + 2 * q, src + (size_t)(first_row + r) * pitch + 4 * q);
+        }
+    }
+}
+
+// x_eos loads: the two absorption spectra rows and the rows of rho, rho0 and
+// B/A are copied into shared memory (cp.async) at the start; c0 and alpha0
+// go to registers and are consumed after the first row transform, so every
+// global load overlaps transform work.
+template <int LOGM>
+struct XEosStage {
+    static constexpr int RPT = XShape<LOGM>::RPT;
+    static constexpr int A = RPT * XStage<LOGM>::SROW;   // one spectrum's rows of a team
+    static constexpr int R = RPT * XShape<LOGM>::M;      // one real field's rows of a team (float2)
+    static constexpr int TEAM = 2 * A + 3 * R;          // per team
+};
+
 template <int LOGM>
 __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_eos_kernel(const XEosK K) {
     using Sh = XShape<LOGM>;
     using St = XStage<LOGM>;
-    constexpr int E = Sh::E, TL = Sh::TL;
-    constexpr int BUF = Sh::RPT * St::SROW;            // one spectrum's rows of a team
+    using Es = XEosStage<LOGM>;
+    constexpr int E = Sh::E, TL = Sh::TL, M = Sh::M;
     extern __shared__ __align__(16) float2 smem[];
     const GridC& g = K.g;
     const Medium& md = K.md;
@@ -515,52 +542,64 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_eos_kernel(con
     const bool valid = row < nrows;
     const int rr = valid ? row : 0;
     typename Sh::Smem S = Sh::row_smem(smem, r);
-    float2* stage = smem + Sh::RPB * Sh::PITCH + team * 2 * BUF;
+    float2* stage = smem + Sh::RPB * Sh::PITCH + team * Es::TEAM;
     const int first = blockIdx.x * Sh::RPB + team * Sh::RPT;
+    const bool nl = md.nonlinear;
     stage_rows<LOGM>(stage, K.a.A1, first, nrows, g.nhp, lane);
-    stage_rows<LOGM>(stage + BUF, K.a.A2, first, nrows, g.nhp, lane);
+    stage_rows<LOGM>(stage + Es::A, K.a.A2, first, nrows, g.nhp, lane);
+    stage_real_rows<LOGM>(stage + 2 * Es::A, K.a.rho_tot, 2 * (size_t)g.nhp, first, nrows, lane);
+    if (nl && md.rho0) stage_real_rows<LOGM>(stage + 2 * Es::A + Es::R, md.rho0, g.nx, first, nrows, lane);
+    if (nl && md.bona) stage_real_rows<LOGM>(stage + 2 * Es::A + 2 * Es::R, md.bona, g.nx, first, nrows, lane);
     cp_async_commit();
     const size_t rb = (size_t)rr * g.nx;
+    const int lr = r % Sh::RPT;                          // this row within the team's stage
     // Eq. 6 with Eq. 8 and Eq. 3:
     //   p = c0^2 (rho + B/2A rho^2/rho0) + c0^2 tau a1 - c0^2 eta a2,
     //   a1 = IFT{k^{y-2} FT{rho0 sum d}}, a2 = IFT{k^{y-1} FT{rho}},
-    //   tau = -2 alpha0 c0^{y-1}, eta = 2 alpha0 c0^y tan(pi y / 2).
-    float2 p0[E], ct[E], ce[E];
-    const float ym1 = md.y - 1.0f;
+    //   tau = -2 alpha0 c0^{y-1}, eta = 2 alpha0 c0^y tan(pi y / 2),
+    // so with ct = c0^2 tau: p = c0^2 (...) + ct (a1 + c0 tan(pi y/2) a2).
+    float2 c[E], al[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-        const int x = 2 * (j + TL * m);
-        const size_t i = rb + x;
-        const float2 rho = valid ? ld2(K.a.rho_tot + (size_t)rr * 2 * g.nhp + x) : make_float2(0.f, 0.f);
-        const float2 c = med2(md.c0, md.c0_s, i);
-        const float2 al = med2(md.alpha0, md.alpha0_s, i);
-        float2 q = rho;
-        if (md.nonlinear) {
-            const float2 r0 = med2(md.rho0, md.rho0_s, i);
-            const float2 ba = med2(md.bona, md.bona_s, i);
-            q.x += __fdividef(0.5f * ba.x * rho.x * rho.x, r0.x);
-            q.y += __fdividef(0.5f * ba.y * rho.y * rho.y, r0.y);
-        }
-        const float cx2 = c.x * c.x, cy2 = c.y * c.y;
-        const float px = exp2f(ym1 * log2f(c.x)), py = exp2f(ym1 * log2f(c.y));   // c0^{y-1}
-        p0[m] = make_float2(cx2 * q.x, cy2 * q.y);
-        ct[m] = make_float2(cx2 * (-2.0f * al.x * px), cy2 * (-2.0f * al.y * py));                 // c0^2 tau
-        ce[m] = make_float2(-cx2 * 2.0f * al.x * px * c.x * md.tan_pi_y_2,
-                            -cy2 * 2.0f * al.y * py * c.y * md.tan_pi_y_2);                        // -c0^2 eta
+        const size_t i = rb + 2 * (j + TL * m);
+        c[m] = med2(md.c0, md.c0_s, i);
+        al[m] = med2(md.alpha0, md.alpha0_s, i);
     }
     cp_async_wait0();
     S.sync();
-    const float2* cur = stage + (r % Sh::RPT) * St::SROW;
+    const float2* cur = stage + lr * St::SROW;
     float2 a[E];
     row_c2r_staged<LOGM>(cur, S, j, g.t.tw, a);
+    const float ym1 = md.y - 1.0f;
+    float2 acc[E], ce[E], c2[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m)
-        p0[m] = make_float2(fmaf(ct[m].x, a[m].x, p0[m].x), fmaf(ct[m].y, a[m].y, p0[m].y));
-    row_c2r_staged<LOGM>(cur + BUF, S, j, g.t.tw, a);
+    for (int m = 0; m < E; ++m) {
+        const float px = exp2f(ym1 * log2f(c[m].x)), py = exp2f(ym1 * log2f(c[m].y));   // c0^{y-1}
+        c2[m] = make_float2(c[m].x * c[m].x, c[m].y * c[m].y);
+        const float2 ct = make_float2(c2[m].x * (-2.0f * al[m].x * px), c2[m].y * (-2.0f * al[m].y * py));
+        acc[m] = make_float2(ct.x * a[m].x, ct.y * a[m].y);
+        ce[m] = make_float2(ct.x * c[m].x * md.tan_pi_y_2, ct.y * c[m].y * md.tan_pi_y_2);   // -c0^2 eta
+    }
+    row_c2r_staged<LOGM>(cur + Es::A, S, j, g.t.tw, a);
+    const float2* rho_s = stage + 2 * Es::A + lr * M;
+    const float2* r0_s = stage + 2 * Es::A + Es::R + lr * M;
+    const float2* ba_s = stage + 2 * Es::A + 2 * Es::R + lr * M;
+    float2 p[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m)
-        p0[m] = make_float2(fmaf(ce[m].x, a[m].x, p0[m].x), fmaf(ce[m].y, a[m].y, p0[m].y));
-    finish_pressure<LOGM>(p0, g, K.sens, K.st, S, j, valid, rr, K.a.P);
+    for (int m = 0; m < E; ++m) {
+        const int e = j + TL * m;
+        const float2 rho = rho_s[e];
+        float2 q = rho;
+        if (nl) {
+            const float2 r0 = md.rho0 ? r0_s[e] : make_float2(md.rho0_s, md.rho0_s);
+            const float2 ba = md.bona ? ba_s[e] : make_float2(md.bona_s, md.bona_s);
+            q.x += __fdividef(0.5f * ba.x * rho.x * rho.x, r0.x);
+            q.y += __fdividef(0.5f * ba.y * rho.y * rho.y, r0.y);
+        }
+        p[m] = make_float2(fmaf(c2[m].x, q.x, fmaf(ce[m].x, a[m].x, acc[m].x)),
+                           fmaf(c2[m].y, q.y, fmaf(ce[m].y, a[m].y, acc[m].y)));
+    }
+    finish_pressure<LOGM>(p, g, K.sens, K.st, S, j, valid, rr, K.a.P);
 }
 
 // ---------------------------------------------------------------- plain x
@@ -680,7 +719,7 @@ cudaError_t launch_x_eos(const GridC& g, const Medium& m, const SensorC& sens,
     XEosK K{g, m, sens, st, a};
     switch (g.lognx - 1) {
 #define CASE(L) \
-    case L: return launch_rows(x_eos_kernel<L>, XShape<L>::RPB, XShape<L>::SMEM + XShape<L>::TPB * XStage<L>::TSTAGE * (int)sizeof(float2), g, K, s);
+    case L: return launch_rows(x_eos_kernel<L>, XShape<L>::RPB, XShape<L>::SMEM + XShape<L>::TPB * XEosStage<L>::TEAM * (int)sizeof(float2), g, K, s);
         KWGB_LOGM_CASES(CASE)
 #undef CASE
     }
