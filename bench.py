@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 1024^3 step and the adjoint measurements")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", type=int, nargs=3, metavar=("NZ", "NY", "NX"), default=None,
+                    help="small case for ncu captures: a heterogeneous nonlinear absorbing medium on an "
+                         "NZ x NY x NX grid stepped --steps times, no timing")
     return ap.parse_args()
 
 
@@ -308,6 +311,10 @@ def run_ours(args):
         out["mixed_f16"] = step_variant(args, kwgb, torch, 3, 8)
         out["mixed_bf16"] = step_variant(args, kwgb, torch, 3, 4)
         out["also_1024"] = step_variant(args, kwgb, torch, 4, 0)
+        out["linear_lossless_512"] = step_variant(args, kwgb, torch, 3, 0, _linear_lossless,
+                                                  "float32, linear lossless (10 FFTs, EOS fused into x_dens)")
+        out["homogeneous_512"] = step_variant(args, kwgb, torch, 3, 0, _homogeneous,
+                                              "float32, homogeneous nonlinear absorbing (scalar medium)")
         out["adjoint"] = adjoint_measure(kwgb, torch)
     if not args.no_extra and world == 1:
         out["cufft_unfused"] = cufft_unfused(args, torch)
@@ -323,12 +330,15 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def step_variant(args, kwgb, torch, cfg_id, extra_flags):
+def step_variant(args, kwgb, torch, cfg_id, extra_flags, modify=None, form=None):
     """Another workload or form, timed like the main line: the 1024^3 workload
-    (same bowl and tissue recipe at 0.1 mm), or the bfloat16-split
-    tensor-core form (extra_flags = 4) of the 512^3 workload."""
+    (same bowl and tissue recipe at 0.1 mm), the float16- / bfloat16-split
+    tensor-core forms (extra_flags = 8 / 4) of the 512^3 workload, or a
+    specialised medium (`modify` edits the configuration)."""
     cfg = inputs.make_config(cfg_id, n_steps=args.warmup + args.steps + 8)
     cfg["flags"] = cfg["flags"] | extra_flags
+    if modify is not None:
+        modify(cfg)
     sim, _ = kwgb.from_config(cfg)
     stream = torch.cuda.current_stream()
     sim.step(args.warmup, stream)
@@ -345,7 +355,7 @@ def step_variant(args, kwgb, torch, cfg_id, extra_flags):
         prof[name] = prof.get(name, 0.0) + t
     bytes_ = sum(kernel_bytes(cfg).get(k, 0) for k in prof)
     peak, _ = measured_peaks()
-    form = {4: "bf16-split tensor-core y/z stages", 8: "f16-split tensor-core y/z stages"}.get(extra_flags, "float32")
+    form = form or {4: "bf16-split tensor-core y/z stages", 8: "f16-split tensor-core y/z stages"}.get(extra_flags, "float32")
     res = {"workload": workload_name(cfg), "form": form,
            "ms_per_step": round(ms, 3),
            "bytes_per_step": bytes_, "frac": round(bytes_ / (ms * 1e-3) / 1e9 / peak, 4),
@@ -353,6 +363,20 @@ def step_variant(args, kwgb, torch, cfg_id, extra_flags):
            "kernels_ms": {k: round(v, 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1])}}
     sim.close()
     return res
+
+
+def _linear_lossless(cfg):
+    """Specialised step: linear, lossless (heterogeneous c0 and rho0 kept)."""
+    cfg["flags"] = 0
+    cfg["alpha0"] = 0.0
+    cfg["bona"] = 0.0
+
+
+def _homogeneous(cfg):
+    """Specialised step: every medium property one scalar (soft tissue)."""
+    cfg["c0"], cfg["rho0"], cfg["bona"] = 1540.0, 1040.0, 7.0
+    cfg["alpha0"] = float(inputs.db_to_neper(0.75, cfg["alpha_power"]))
+    cfg["c_ref"] = 1540.0
 
 
 def adjoint_measure(kwgb, torch):
@@ -572,8 +596,38 @@ def e2e(args, cfg, kwgb, torch):
                     "read of every sensor output, per step" % args.steps}
 
 
+def run_profile_case(args):
+    """A small grid with the kernels of the benchmark (same row and line
+    lengths along the transformed axes), for `ncu --set full` captures that
+    must stay a few GB: smooth random c0, rho0, B/A, alpha0 (y = 1.1), a
+    Gaussian initial pressure, a PML of 10 cells and a 9^3 sensor box."""
+    import torch
+    from paper_1408_4675_gb300 import build, kwgb
+    build.build()
+    kwgb.load()
+    shape = tuple(args.profile_case)
+    d = 1e-4
+    c0 = inputs.smooth_random_field(shape, 1450.0, 1650.0, 11, 3.0)
+    rho0 = inputs.smooth_random_field(shape, 950.0, 1100.0, 12, 3.0)
+    bona = inputs.smooth_random_field(shape, 5.0, 9.0, 13, 3.0)
+    alpha0 = inputs.db_to_neper(inputs.smooth_random_field(shape, 0.3, 1.0, 14, 3.0), 1.1)
+    c_ref = float(c0.max())
+    sim = kwgb.Simulation(shape, (d, d, d), 0.3 * d / c_ref, c_ref, (10, 10, 10), (2.0, 2.0, 2.0),
+                          flags=3, alpha_power=1.1)
+    sim.set_medium(c0, rho0, bona, alpha0)
+    sim.set_initial_pressure(inputs.gaussian_ball(shape, 3.0, 1e5))
+    sim.add_sensor(inputs.box_mask(shape, tuple(n // 2 for n in shape), 4), 3)
+    sim.step(args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": list(shape), "steps": args.steps, "status": sim.status()}))
+    sim.close()
+
+
 def main():
     args = parse()
+    if args.profile_case is not None:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

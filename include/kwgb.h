@@ -213,10 +213,11 @@ int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const float* in, fl
 
 /* Gradient of an objective of the pressure with respect to every source
  * signal sample, by a hand-written adjoint (reverse-mode) of the time step
- * (Eqs. 4a-4d and 6 run backwards: the transpose of the Eq. 4a operator is
- * minus the Eq. 4c operator and vice versa; Eq. 4d and Eq. 6 by their
- * pointwise derivatives).  The paper has no adjoint; this is the
- * differentiation form built on its step.
+ * (Eqs. 4a-4d, 6 and 8 run backwards: the transpose of the Eq. 4a operator
+ * is minus the Eq. 4c operator and vice versa; the k^{y-2} and k^{y-1}
+ * operators of Eq. 8 are real and even, hence their own transposes; Eq. 4d
+ * and Eq. 6 by their pointwise derivatives).  The paper has no adjoint; this
+ * is the differentiation form built on its step.
  *   obj_idx    n_obj unique linear indices (host) of the objective region
  *   objective  KWGB_OBJ_MEAN_ABS_P (d|p|/dp taken as sign(p))
  *   n_steps    steps of the run (the simulation must not have stepped yet)
@@ -228,11 +229,38 @@ int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const float* in, fl
  *              n_signals rows of n_t values dJ/dsignal[row][n]
  * On return the simulation holds the forward end state (n_steps taken) and
  * its sensors hold the forward run's outputs.  Synchronises.
- * Errors: ARG, STATE (already stepped), UNSUPPORTED (absorbing medium),
- * OOM, CUDA, NONFINITE. */
+ * Errors: ARG, STATE (already stepped), OOM, CUDA, NONFINITE. */
 int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
                  int64_t n_steps, int64_t checkpoint_every, double* J_out, double* grad_out,
                  int64_t grad_len, void* cuda_stream);
+
+/* ---- checkpoint / restart of a run -------------------------------------
+ * A snapshot holds everything a step reads and writes: u_xi, rho_xi, the
+ * x-transformed pressure spectrum, every sensor accumulator (p_max, sum of
+ * p^2, last p at masked points, full-grid maps, intensity sums) and the step
+ * index.  Continuing from a snapshot is bitwise identical to not having
+ * stopped.  The paper's code splits long runs into phases by saving the
+ * time-varying fields and the aggregated outputs and reloading them
+ * (Sec. 3.4, simulation stages); these calls are that facility for one GPU,
+ * with the file I/O left to the caller.
+ * The grid, medium, sources and sensors are not part of the snapshot: a
+ * restore needs a simulation created and set up the same way (same
+ * descriptor, medium, sources and sensors in the same order).  The first of
+ * these calls freezes the source and sensor lists, as kwgb_step does. */
+
+/* Bytes of a snapshot of sim (0 on error). */
+int64_t kwgb_state_bytes(kwgb_sim* sim);
+
+/* Copy the state into host memory buf (len >= kwgb_state_bytes bytes,
+ * caller-owned).  Synchronises the device.  Errors: ARG (null or short
+ * buffer), STATE (no medium), CUDA. */
+int kwgb_save_state(kwgb_sim* sim, void* buf, int64_t len);
+
+/* Restore a snapshot written by kwgb_save_state (buf is read only; len its
+ * size).  The snapshot's grid and sensor layout must match sim's, else ARG;
+ * the device status flag is cleared.  Synchronises.  Errors: ARG, STATE,
+ * CUDA. */
+int kwgb_load_state(kwgb_sim* sim, const void* buf, int64_t len);
 
 /* Number of steps taken so far. */
 int64_t kwgb_steps_done(const kwgb_sim* sim);

@@ -52,6 +52,12 @@ the same readings, written independently):
      last term needs u^{Nt+1/2}: it is computed at read time by one extra
      velocity update that is not stored.
  R13 With no step taken: p_max = -inf, p_rms = 0, I = 0.
+ R14 Time-series outputs (the paper's code stores aggregates such as the
+     peak positive and negative pressure, and time-varying p and u at the
+     sensor points, Sec. 3.4): p_min = min_n p^n (+inf with no step);
+     the p series holds p^1 .. p^Nt at the sensor points, the u series
+     u_xi^{1/2} .. u_xi^{Nt-1/2} (the value at the staggered point i + 1/2
+     as stored, no averaging), both ordered [n][point] and [n][xi][point].
 """
 
 import os
@@ -65,6 +71,9 @@ ABSORBING = 2
 P_MAX = 1
 P_RMS = 2
 I_AVG = 4
+P_MIN = 8
+P_SERIES = 16
+U_SERIES = 32
 
 ADDITIVE_MASS = 0
 
@@ -279,8 +288,8 @@ class Simulation:
             idx = np.arange(self.p.size, dtype=np.int64)
         idx = np.asarray(idx, dtype=np.int64)
         m = len(idx)
-        s = dict(idx=idx, record=record, p_max=np.full(m, -np.inf), p2=np.zeros(m),
-                 I=np.zeros((3, m)), count=0)
+        s = dict(idx=idx, record=record, p_max=np.full(m, -np.inf), p_min=np.full(m, np.inf), p2=np.zeros(m),
+                 I=np.zeros((3, m)), count=0, p_series=[], u_series=[])
         self.sensors.append(s)
         return len(self.sensors) - 1
 
@@ -350,8 +359,13 @@ class Simulation:
         for s in self.sensors:
             v = pf[s["idx"]]
             s["p_max"] = np.maximum(s["p_max"], v)
+            s["p_min"] = np.minimum(s["p_min"], v)
             s["p2"] += v * v
             s["count"] += 1
+            if s["record"] & P_SERIES:
+                s["p_series"].append(v.copy())
+            if s["record"] & U_SERIES:                         # u^{n+1/2} of this step (R14)
+                s["u_series"].append(np.stack([u.reshape(-1)[s["idx"]] for u in self.u]))
 
     # -- outputs ----------------------------------------------------------
     def read(self, sensor_id, which):
@@ -359,6 +373,12 @@ class Simulation:
         nt = s["count"]
         if which == P_MAX:
             return s["p_max"].copy()
+        if which == P_MIN:
+            return s["p_min"].copy()
+        if which == P_SERIES:
+            return np.array(s["p_series"]).reshape(len(s["p_series"]), len(s["idx"]))
+        if which == U_SERIES:
+            return np.array(s["u_series"]).reshape(len(s["u_series"]), 3, len(s["idx"]))
         if which == P_RMS:
             return np.sqrt(s["p2"] / nt) if nt else np.zeros_like(s["p2"])
         if which == I_AVG:

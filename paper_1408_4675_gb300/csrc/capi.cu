@@ -92,6 +92,12 @@ struct kwgb_sim {
     cudaStream_t last_stream = nullptr;
     int64_t launches = 0;       // kernels launched so far
     bool adjoint_done = false;
+    // one captured step, replayed by kwgb_step (CUDA graph)
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;         // stream the step is captured on
+    int64_t glaunches = 0;              // kernels in the captured step
+    bool graph_off = false;             // capture not possible: launch directly
+    bool warmed = false;                // a step has run directly (one-time set-up done)
     // per-launch event timing (kwgb_step_profiled)
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -452,6 +458,56 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
     return KWGB_OK;
 }
 
+// Capture one step into a CUDA graph (once; every launch argument of a step
+// is fixed after freeze(), and the time-dependent parts read the device step
+// counter), so that a step is one graph launch instead of 13-15 kernel
+// launches.  Called after the first step has run directly (one-time kernel
+// attribute set-up stays outside the capture).  If capture or instantiation
+// fails the simulation keeps launching kernels directly.
+static void capture_step(kwgb_sim* sim) {
+    if (sim->gexec || sim->graph_off) return;
+    sim->graph_off = true;
+    if (!sim->cap && cudaStreamCreateWithFlags(&sim->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cudaStreamBeginCapture(sim->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const int64_t l0 = sim->launches;
+    const bool prof = sim->prof;
+    const std::string err = sim->err;
+    sim->prof = false;
+    const int e = launch_step(sim, sim->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(sim->cap, &graph);
+    sim->prof = prof;
+    sim->glaunches = sim->launches - l0;
+    sim->launches = l0;
+    sim->err = err;
+    if (e == KWGB_OK && ce == cudaSuccess && graph &&
+        cudaGraphInstantiate(&sim->gexec, graph, 0) == cudaSuccess)
+        sim->graph_off = false;
+    else
+        sim->gexec = nullptr;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+}
+
+// One step on stream s: the captured graph when there is one, else direct launches.
+static int run_step(kwgb_sim* sim, cudaStream_t s) {
+    if (sim->warmed && !sim->prof) capture_step(sim);
+    if (sim->gexec && !sim->prof) {
+        CK(cudaGraphLaunch(sim->gexec, s));
+        sim->launches += sim->glaunches;
+        return KWGB_OK;
+    }
+    const int e = launch_step(sim, s);
+    if (e == KWGB_OK) sim->warmed = true;
+    return e;
+}
+
 // ------------------------------------------------------------------ initial pressure
 extern "C" int kwgb_set_initial_pressure(kwgb_sim* sim, const float* p0) {
     if (!sim) return KWGB_ERR_ARG;
@@ -658,9 +714,103 @@ extern "C" int kwgb_step(kwgb_sim* sim, int64_t n_steps, void* cuda_stream) {
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     sim->last_stream = s;
     for (int64_t i = 0; i < n_steps; ++i) {
-        if (int e = launch_step(sim, s)) return e;
+        if (int e = run_step(sim, s)) return e;
         sim->steps++;
     }
+    return KWGB_OK;
+}
+
+// ------------------------------------------------------------------ checkpoint / restart
+namespace {
+struct StateHeader {
+    char magic[8];
+    int64_t nx, ny, nz, nhp, n_slots, nfull, n_i, steps, bytes;
+};
+constexpr char kStateMagic[8] = {'K', 'W', 'G', 'B', 'S', 'T', '0', '1'};
+}  // namespace
+
+// The device blocks of a snapshot, in order.
+static std::vector<std::pair<void*, size_t>> state_blocks(kwgb_sim* sim) {
+    std::vector<std::pair<void*, size_t>> b;
+    const size_t F = (size_t)sim->N * sizeof(float);
+    for (int a = 0; a < 3; ++a) b.push_back({sim->u[a], F});
+    for (int a = 0; a < 3; ++a) b.push_back({sim->rho[a], F});
+    b.push_back({sim->P, sim->spec_elems * sizeof(float2)});
+    const SensorC& sc = sim->sens;
+    if (sim->n_slots) {
+        b.push_back({sc.p_max, sim->n_slots * sizeof(float)});
+        b.push_back({sc.p2, sim->n_slots * sizeof(double)});
+        b.push_back({sc.p_sens, sim->n_slots * sizeof(float)});
+    }
+    for (int k = 0; k < sc.nfull; ++k) {
+        b.push_back({sc.full_max[k], (size_t)sim->N * sizeof(float)});
+        b.push_back({sc.full_p2[k], (size_t)sim->N * sizeof(double)});
+    }
+    if (sim->n_i) b.push_back({sim->I, 3 * sim->n_i * sizeof(double)});
+    return b;
+}
+
+static int64_t state_size(kwgb_sim* sim) {
+    int64_t n = sizeof(StateHeader);
+    for (auto& b : state_blocks(sim)) n += (int64_t)b.second;
+    return n;
+}
+
+static StateHeader state_header(kwgb_sim* sim) {
+    StateHeader h;
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.nx = sim->g.nx; h.ny = sim->g.ny; h.nz = sim->g.nz; h.nhp = sim->g.nhp;
+    h.n_slots = sim->n_slots; h.nfull = sim->sens.nfull; h.n_i = sim->n_i;
+    h.steps = sim->steps;
+    h.bytes = state_size(sim);
+    return h;
+}
+
+extern "C" int64_t kwgb_state_bytes(kwgb_sim* sim) {
+    if (!sim || !sim->medium_set) return 0;
+    if (freeze(sim)) return 0;
+    return state_size(sim);
+}
+
+extern "C" int kwgb_save_state(kwgb_sim* sim, void* buf, int64_t len) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
+    if (int e = freeze(sim)) return e;
+    const StateHeader h = state_header(sim);
+    if (!buf || len < h.bytes) return fail(sim, KWGB_ERR_ARG, "state buffer too small");
+    CK(cudaDeviceSynchronize());
+    char* out = static_cast<char*>(buf);
+    std::memcpy(out, &h, sizeof(h));
+    size_t off = sizeof(h);
+    for (auto& b : state_blocks(sim)) {
+        CK(cudaMemcpy(out + off, b.first, b.second, cudaMemcpyDeviceToHost));
+        off += b.second;
+    }
+    return KWGB_OK;
+}
+
+extern "C" int kwgb_load_state(kwgb_sim* sim, const void* buf, int64_t len) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
+    if (int e = freeze(sim)) return e;
+    if (!buf || len < (int64_t)sizeof(StateHeader)) return fail(sim, KWGB_ERR_ARG, "not a snapshot");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    const StateHeader mine = state_header(sim);
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0) return fail(sim, KWGB_ERR_ARG, "not a snapshot");
+    if (h.nx != mine.nx || h.ny != mine.ny || h.nz != mine.nz || h.nhp != mine.nhp || h.n_slots != mine.n_slots ||
+        h.nfull != mine.nfull || h.n_i != mine.n_i || h.bytes != mine.bytes || len < h.bytes || h.steps < 0)
+        return fail(sim, KWGB_ERR_ARG, "snapshot of a different grid or sensor layout");
+    CK(cudaDeviceSynchronize());
+    const char* in = static_cast<const char*>(buf);
+    size_t off = sizeof(h);
+    for (auto& b : state_blocks(sim)) {
+        CK(cudaMemcpy(b.first, in + off, b.second, cudaMemcpyHostToDevice));
+        off += b.second;
+    }
+    CK(cudaMemcpy(sim->d_step, &h.steps, sizeof(int64_t), cudaMemcpyHostToDevice));
+    CK(cudaMemset(sim->d_flag, 0, sizeof(int)));
+    sim->steps = h.steps;
     return KWGB_OK;
 }
 
@@ -865,6 +1015,20 @@ static int adj_chain(kwgb_sim* sim, float* const in[3], float* const out[3], int
     return KWGB_OK;
 }
 
+// q1 <- IFT{k^{y-2} FT{q1}}, q2 <- IFT{k^{y-1} FT{q2}} (real fields, in place)
+static int adj_abs_chain(kwgb_sim* sim, float* q1, float* q2, cudaStream_t s) {
+    const GridC& g = sim->g;
+    float2* sp[3] = {sim->T1, sim->T2, nullptr};
+    LK(launch_x_r2c(g, q1, g.nx, sim->T1, s));
+    LK(launch_x_r2c(g, q2, g.nx, sim->T2, s));
+    LK(ypass(sim, -1, sp, sp, 2, s));
+    LK(zop(sim, Z_ABS, sp, sp, s));
+    LK(ypass(sim, +1, sp, sp, 2, s));
+    LK(launch_x_c2r(g, sim->T1, q1, g.nx, s));
+    LK(launch_x_c2r(g, sim->T2, q2, g.nx, s));
+    return KWGB_OK;
+}
+
 static int copy_dev(kwgb_sim* sim, void* dst, const void* src, size_t bytes, cudaStream_t s) {
     CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
     return KWGB_OK;
@@ -877,7 +1041,6 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
     if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
     if (sim->steps != 0 || sim->frozen || sim->adjoint_done)
         return fail(sim, KWGB_ERR_STATE, "kwgb_adjoint needs a simulation that has not stepped");
-    if (sim->md.absorbing) return fail(sim, KWGB_ERR_UNSUPPORTED, "the adjoint serves lossless media");
     if (objective != KWGB_OBJ_MEAN_ABS_P) return fail(sim, KWGB_ERR_ARG, "unknown objective");
     if (!obj_idx || n_obj <= 0 || n_steps <= 0 || checkpoint_every <= 0 || !J_out)
         return fail(sim, KWGB_ERR_ARG, "bad objective, step count or checkpoint interval");
@@ -914,7 +1077,9 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
     char* ck = static_cast<char*>(dalloc(sim, (size_t)nck * (6 * F + SB)));
     char* fin = static_cast<char*>(dalloc(sim, 6 * F + SB));
     float* seg = static_cast<float*>(dalloc(sim, (size_t)(segK + 1) * 6 * F));
-    float* lam = static_cast<float*>(dalloc(sim, 11 * F));
+    const bool absorbing = sim->md.absorbing != 0;
+    const int nlam = absorbing ? 13 : 11;
+    float* lam = static_cast<float*>(dalloc(sim, nlam * F));
     float* pobj = static_cast<float*>(dalloc(sim, (size_t)n_steps * n_obj * sizeof(float)));
     double* grad = static_cast<double*>(dalloc(sim, (size_t)std::max<int64_t>(rows, 1) * max_nt * sizeof(double)));
     if (!ck || !fin || !seg || !lam || !pobj || !grad) return fail(sim, KWGB_ERR_OOM, "adjoint buffers");
@@ -968,7 +1133,7 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
     for (int64_t n = 0; n < n_steps; ++n) {
         if (n % K == 0)
             if (int e = save_state(ck + (size_t)(n / K) * (6 * F + SB))) return e;
-        if (int e = launch_step(sim, s)) return e;
+        if (int e = run_step(sim, s)) return e;
         sim->steps++;
         if (int e = copy_dev(sim, pobj + n * n_obj, sim->sens.p_sens + slot0, n_obj * sizeof(float), s)) return e;
     }
@@ -1006,7 +1171,7 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
     for (float v : hp) J += std::fabs((double)v);
     *J_out = J * w;
     // ---- reverse pass
-    CK(cudaMemsetAsync(lam, 0, 11 * F, s));
+    CK(cudaMemsetAsync(lam, 0, nlam * F, s));
     CK(cudaMemsetAsync(grad, 0, (size_t)std::max<int64_t>(rows, 1) * max_nt * sizeof(double), s));
     AdjFields af{};
     af.lam_p = lam;
@@ -1016,6 +1181,10 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
         af.w[a] = lam + (8 + a) * N;
     }
     af.lam_src = lam + 7 * N;
+    float* q1 = absorbing ? lam + 11 * N : nullptr;
+    float* q2 = absorbing ? lam + 12 * N : nullptr;
+    af.abs1 = q1;
+    af.abs2 = q2;
     const GridC& g = sim->g;
     auto seg_rho = [&](int64_t k, int a) { return seg + ((size_t)k * 6 + a) * N; };
     auto seg_u = [&](int64_t k, int a) { return seg + ((size_t)k * 6 + 3 + a) * N; };
@@ -1025,7 +1194,7 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
         for (int64_t n = n0; n < n1; ++n) {
             for (int a = 0; a < 3; ++a)
                 if (int e = copy_dev(sim, seg_rho(n - n0, a), sim->rho[a], F, s)) return e;
-            if (int e = launch_step(sim, s)) return e;
+            if (int e = run_step(sim, s)) return e;
             for (int a = 0; a < 3; ++a)
                 if (int e = copy_dev(sim, seg_u(n - n0, a), sim->u[a], F, s)) return e;
         }
@@ -1034,6 +1203,10 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
         for (int64_t n = n1 - 1; n >= n0; --n) {
             const int64_t k = n - n0;
             LK(launch_adj_obj(n_obj, d_obj, pobj + n * n_obj, w, af.lam_p, s));
+            if (absorbing) {                                                      // Eq. 8 backwards
+                LK(launch_adj_absprep(g, sim->md, af.lam_p, q1, q2, s));
+                if (int e = adj_abs_chain(sim, q1, q2, s)) return e;
+            }
             float* uin[3] = {seg_u(k, 0), seg_u(k, 1), seg_u(k, 2)};
             if (int e = adj_chain(sim, uin, af.w, Z_DIV, s)) return e;               // d_xi (Eq. 4c)
             for (int a = 0; a < 3; ++a) {
@@ -1077,6 +1250,8 @@ extern "C" const char* kwgb_last_error(const kwgb_sim* sim) {
 extern "C" void kwgb_destroy(kwgb_sim* sim) {
     if (!sim) return;
     if (sim->medium_set) cudaDeviceSynchronize();
+    if (sim->gexec) cudaGraphExecDestroy(sim->gexec);
+    if (sim->cap) cudaStreamDestroy(sim->cap);
     for (void* p : sim->allocs) {
         if (sim->freef) sim->freef(p, sim->actx);
         else cudaFree(p);

@@ -12,7 +12,12 @@
 //   lambda_u_xi  <- f_sg^2 lambda_u_xi'                               (Eq. 4b)
 //   lambda_g_xi   = -f_sg dt / rho0_sg lambda_u_xi'
 //   lambda_p      = -sum_xi (Eq. 4c op) lambda_g_xi
-// (linear medium: no (B/A) term and a denominator of 1).
+// (linear medium: no (B/A) term and a denominator of 1).  Absorbing medium
+// (Eq. 8, p gains c0^2 tau a1 - c0^2 eta a2 with a1 = IFT{k^{y-2} FT{rho0
+// sum d}}, a2 = IFT{k^{y-1} FT{rho}}): the two operators are real and even,
+// hence self-adjoint, so
+//   lambda_rho   += IFT{k^{y-1} FT{-c0^2 eta lambda_p}}            (abs2)
+//   lambda_d_xi  += rho0 IFT{k^{y-2} FT{c0^2 tau lambda_p}}         (rho0 abs1)
 #include "kwgb_internal.h"
 
 namespace kwgb {
@@ -30,6 +35,11 @@ __global__ void adj_dens_kernel(GridC g, Medium md, AdjFields a) {
             const float rho = a.rho_after[0][i] + a.rho_after[1][i] + a.rho_after[2][i];
             lrt *= 1.0f + medv(md.bona, md.bona_s, i) * rho / r0;
         }
+        float ld_abs = 0.f;
+        if (a.abs1) {
+            lrt += a.abs2[i];
+            ld_abs = r0 * a.abs1[i];
+        }
         float src = 0.f;
 #pragma unroll
         for (int xi = 0; xi < 3; ++xi) {
@@ -40,13 +50,26 @@ __global__ void adj_dens_kernel(GridC g, Medium md, AdjFields a) {
             if (md.nonlinear) {
                 const float den = 1.0f + 2.0f * g.dt * d;
                 a.lam_rho[xi][i] = lrp * f * f / den;
-                a.w[xi][i] = -lrp * f * g.dt * (r0 + 2.0f * f * a.rho_before[xi][i]) / (den * den);
+                a.w[xi][i] = ld_abs - lrp * f * g.dt * (r0 + 2.0f * f * a.rho_before[xi][i]) / (den * den);
             } else {
                 a.lam_rho[xi][i] = lrp * f * f;
-                a.w[xi][i] = -lrp * f * g.dt * r0;
+                a.w[xi][i] = ld_abs - lrp * f * g.dt * r0;
             }
         }
         a.lam_src[i] = src;
+    }
+}
+
+__global__ void adj_absprep_kernel(GridC g, Medium md, const float* __restrict__ lam_p, float* q1, float* q2) {
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    const float ym1 = md.y - 1.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float c = medv(md.c0, md.c0_s, i);
+        const float al = medv(md.alpha0, md.alpha0_s, i);
+        const float ct = c * c * (-2.0f * al * exp2f(ym1 * log2f(c)));    // c0^2 tau, tau = -2 alpha0 c0^{y-1}
+        const float l = lam_p[i];
+        q1[i] = ct * l;
+        q2[i] = ct * c * md.tan_pi_y_2 * l;                               // -c0^2 eta = c0^2 tau c0 tan(pi y/2)
     }
 }
 
@@ -107,6 +130,12 @@ static int blocks_for(int64_t n) {
 
 cudaError_t launch_adj_dens(const GridC& g, const Medium& m, const AdjFields& a, cudaStream_t s) {
     adj_dens_kernel<<<blocks_for((int64_t)g.nx * g.ny * g.nz), 256, 0, s>>>(g, m, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_absprep(const GridC& g, const Medium& m, const float* lam_p, float* q1, float* q2,
+                               cudaStream_t s) {
+    adj_absprep_kernel<<<blocks_for((int64_t)g.nx * g.ny * g.nz), 256, 0, s>>>(g, m, lam_p, q1, q2);
     return cudaGetLastError();
 }
 

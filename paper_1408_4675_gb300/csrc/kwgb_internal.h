@@ -166,8 +166,13 @@ struct AdjFields {
     float* w[3];              // work: d_xi -> lambda_d_xi -> (Eq. 4a op) -> lambda_g_xi -> ...
     const float* rho_before[3];
     const float* rho_after[3];
+    const float* abs1;        // absorbing: IFT{k^{y-2} FT{c0^2 tau lambda_p}} (else null)
+    const float* abs2;        //            IFT{k^{y-1} FT{-c0^2 eta lambda_p}}
 };
-// Eq. 6 and Eq. 4d backwards (lossless): lambda_rho_xi, lambda_d_xi (into w), lambda_src
+// Eq. 8 backwards, first half: q1 = c0^2 tau lambda_p, q2 = -c0^2 eta lambda_p
+cudaError_t launch_adj_absprep(const GridC& g, const Medium& m, const float* lam_p, float* q1, float* q2,
+                               cudaStream_t s);
+// Eq. 6 (and Eq. 8) and Eq. 4d backwards: lambda_rho_xi, lambda_d_xi (into w), lambda_src
 cudaError_t launch_adj_dens(const GridC& g, const Medium& m, const AdjFields& a, cudaStream_t s);
 // Eq. 4b backwards: w holds D_f lambda_d on entry and lambda_g on exit; lambda_u updated
 cudaError_t launch_adj_vel(const GridC& g, const Medium& m, const AdjFields& a, cudaStream_t s);

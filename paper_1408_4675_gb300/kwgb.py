@@ -84,6 +84,12 @@ def load():
     L.kwgb_kernel_name.restype = ctypes.c_char_p
     L.kwgb_adjoint.argtypes = [vp, vp, i64, ctypes.c_int, i64, i64, ctypes.POINTER(ctypes.c_double), vp, i64, vp]
     L.kwgb_adjoint.restype = ctypes.c_int
+    L.kwgb_state_bytes.argtypes = [vp]
+    L.kwgb_state_bytes.restype = i64
+    L.kwgb_save_state.argtypes = [vp, vp, i64]
+    L.kwgb_save_state.restype = ctypes.c_int
+    L.kwgb_load_state.argtypes = [vp, vp, i64]
+    L.kwgb_load_state.restype = ctypes.c_int
     L.kwgb_destroy.argtypes = [vp]
     L.kwgb_destroy.restype = None
     for name in ("kwgb_create", "kwgb_set_allocator", "kwgb_set_medium", "kwgb_set_initial_pressure",
@@ -232,6 +238,22 @@ class Simulation:
     @property
     def steps_done(self):
         return self.L.kwgb_steps_done(self.h)
+
+    def save_state(self):
+        """Snapshot of the run (fields, sensor accumulators, step index) as a
+        bytes-like uint8 array (kwgb_save_state)."""
+        n = self.L.kwgb_state_bytes(self.h)
+        if n <= 0:
+            raise KwgbError(-6, self.L.kwgb_last_error(self.h).decode())
+        buf = np.empty(n, dtype=np.uint8)
+        self._check(self.L.kwgb_save_state(self.h, _ptr(buf), n))
+        return buf
+
+    def load_state(self, buf):
+        """Restore a snapshot from save_state (kwgb_load_state)."""
+        buf = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if not isinstance(buf, np.ndarray) else buf,
+                                   dtype=np.uint8)
+        self._check(self.L.kwgb_load_state(self.h, _ptr(buf), buf.size))
 
     def read(self, sensor_id, which):
         n = self._sensors[sensor_id] * (3 if which == I_AVG else 1)

@@ -86,3 +86,16 @@ def test_state_errors_without_device(lib):
     assert b"n_steps" in lib.kwgb_last_error(h)
     lib.kwgb_destroy(h)
     lib.kwgb_destroy(None)
+
+
+def test_snapshot_calls_without_device(lib):
+    h = ctypes.c_void_p()
+    assert lib.kwgb_create(ctypes.byref(_desc()), ctypes.byref(h)) == 0
+    lib.kwgb_state_bytes.restype = ctypes.c_int64
+    assert lib.kwgb_state_bytes(h) == 0                      # no medium yet
+    buf = ctypes.create_string_buffer(64)
+    assert lib.kwgb_save_state(h, buf, ctypes.c_int64(64)) == -6
+    assert lib.kwgb_load_state(h, buf, ctypes.c_int64(64)) == -6
+    assert lib.kwgb_save_state(None, buf, ctypes.c_int64(64)) == -1
+    lib.kwgb_destroy(h)
+

@@ -47,9 +47,9 @@ def test_dot_product_identity_linear(flags):
     assert abs(J - dot) <= 1e-12 * abs(J), (J, dot)
 
 
-def _phased_run(phases, amps, with_grad, nonlinear_backward=True):
+def _phased_run(phases, amps, with_grad, nonlinear_backward=True, flags=oracle.NONLINEAR):
     nt = 30
-    sim = _small_sim(oracle.NONLINEAR, seed=7, shape=(12, 12, 12))
+    sim = _small_sim(flags, seed=7, shape=(12, 12, 12))
     f0 = 1.5e6
     elems = [np.array([13 + 12 * (12 * 3 + 5) + k for k in range(3)]),
              np.array([20 + 12 * (12 * 3 + 7) + k for k in range(3)])]
@@ -63,7 +63,7 @@ def _phased_run(phases, amps, with_grad, nonlinear_backward=True):
     if not with_grad:
         return J
     if not nonlinear_backward:
-        sim.g.flags = 0
+        sim.g.flags = flags & ~oracle.NONLINEAR
     grads = adjoint.backward(sim, rec, dJdp)
     dphi = np.array([(gr.sum(axis=0) * a * np.cos(2 * np.pi * f0 * t + ph)).sum()
                      for gr, a, ph in zip(grads, amps, phases)])
@@ -72,20 +72,22 @@ def _phased_run(phases, amps, with_grad, nonlinear_backward=True):
     return J, dphi, damp
 
 
-def test_finite_differences_nonlinear():
+@pytest.mark.parametrize("flags", [oracle.NONLINEAR, oracle.NONLINEAR | oracle.ABSORBING])
+def test_finite_differences_nonlinear(flags):
     phases = np.array([0.3, -0.7])
     amps = np.array([3e7, 2e7])          # strong enough that the nonlinear terms matter
-    J, dphi, damp = _phased_run(phases, amps, True)
+    run = lambda ph, am, wg, nb=True: _phased_run(ph, am, wg, nb, flags)
+    J, dphi, damp = run(phases, amps, True)
     h = 1e-6
     for e in range(2):
         dp = np.zeros(2)
         dp[e] = h
-        fd = (_phased_run(phases + dp, amps, False) - _phased_run(phases - dp, amps, False)) / (2 * h)
+        fd = (run(phases + dp, amps, False) - run(phases - dp, amps, False)) / (2 * h)
         assert abs(fd - dphi[e]) <= 1e-6 * abs(fd), (e, fd, dphi[e])
         da = np.zeros(2)
         da[e] = h * amps[e]
-        fda = (_phased_run(phases, amps + da, False) - _phased_run(phases, amps - da, False)) / (2 * h * amps[e])
+        fda = (run(phases, amps + da, False) - run(phases, amps - da, False)) / (2 * h * amps[e])
         assert abs(fda - damp[e]) <= 1e-6 * abs(fda), (e, fda, damp[e])
     # the nonlinear terms of the backward pass matter at this amplitude
-    _, dphi_lin, _ = _phased_run(phases, amps, True, nonlinear_backward=False)
+    _, dphi_lin, _ = run(phases, amps, True, False)
     assert np.abs(dphi_lin - dphi).max() > 1e-4 * np.abs(dphi).max()

@@ -1,5 +1,5 @@
-"""Brute-force pins of the oracle's sensor outputs (p_max, p_rms, time-averaged
-intensity) on a tiny grid: every sample is taken from the stepped fields one
+"""Brute-force pins of the oracle's sensor outputs (p_max, p_min, p_rms,
+time-averaged intensity, p and u time series) on a tiny grid: every sample is taken from the stepped fields one
 step at a time and combined by explicit loops, and the last velocity
 u^{Nt+1/2} comes from actually taking one more step on a copy."""
 
@@ -32,7 +32,8 @@ def test_sensor_outputs_brute_force():
     sim = _tiny_sim()
     nx, ny, nz = sim.g.n
     pts = [0, 5, 47, nx * ny * nz - 1, 123]            # includes wrap-around neighbours
-    sid = sim.add_sensor(np.array(pts), oracle.P_MAX | oracle.P_RMS | oracle.I_AVG)
+    sid = sim.add_sensor(np.array(pts), oracle.P_MAX | oracle.P_RMS | oracle.I_AVG | oracle.P_MIN
+                         | oracle.P_SERIES | oracle.U_SERIES)
     ref = copy.deepcopy(sim)
     nt = 5
     # p_hist[n-1] = p^n; u_hist[m] = u^{m-1/2}
@@ -60,12 +61,21 @@ def test_sensor_outputs_brute_force():
         return 0.5 * (u[xi][zm, ym, xm] + u[xi][z, y, x])
 
     pmax = sim.read(sid, oracle.P_MAX)
+    pmin = sim.read(sid, oracle.P_MIN)
     prms = sim.read(sid, oracle.P_RMS)
     inten = sim.read(sid, oracle.I_AVG)
+    pser = sim.read(sid, oracle.P_SERIES)
+    user = sim.read(sid, oracle.U_SERIES)
+    assert pser.shape == (nt, len(pts)) and user.shape == (nt, 3, len(pts))
     for j, i in enumerate(pts):
         x, y, z = coords(i)
         samples = [p_hist[n][z, y, x] for n in range(nt)]
         assert abs(pmax[j] - max(samples)) <= 1e-13 * max(abs(v) for v in samples)
+        assert pmin[j] == min(samples)
+        for n in range(nt):                  # p^{n+1} and u^{n+1/2} after step n
+            assert pser[n, j] == p_hist[n][z, y, x]
+            for xi in range(3):
+                assert user[n, xi, j] == u_hist[n + 1][xi][z, y, x]
         rms = (sum(v * v for v in samples) / nt) ** 0.5
         assert abs(prms[j] - rms) <= 1e-13 * rms
         for xi in range(3):
@@ -79,7 +89,8 @@ def test_sensor_outputs_brute_force():
 
 def test_sensors_before_any_step():
     sim = _tiny_sim()
-    sid = sim.add_sensor(None, oracle.P_MAX | oracle.P_RMS | oracle.I_AVG)
+    sid = sim.add_sensor(None, oracle.P_MAX | oracle.P_RMS | oracle.I_AVG | oracle.P_MIN)
     assert np.all(np.isneginf(sim.read(sid, oracle.P_MAX)))
+    assert np.all(np.isposinf(sim.read(sid, oracle.P_MIN)))
     assert np.all(sim.read(sid, oracle.P_RMS) == 0)
     assert np.all(sim.read(sid, oracle.I_AVG) == 0)
