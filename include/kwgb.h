@@ -56,9 +56,17 @@ extern "C" {
 #define KWGB_P_MAX  1u   /* max_n p^n, n = 1..Nt                               */
 #define KWGB_P_RMS  2u   /* sqrt(mean_n (p^n)^2)                               */
 #define KWGB_I_AVG  4u   /* time-averaged intensity, 3 components per point    */
+#define KWGB_P_MIN  8u   /* min_n p^n (peak negative pressure)                 */
+#define KWGB_P_SERIES 16u /* p^n at every step (ring of the last `capacity`    */
+                          /* steps, see kwgb_set_series_capacity)              */
+#define KWGB_U_SERIES 32u /* u_x, u_y, u_z^{n-1/2} at every step (same ring;   */
+                          /* the value at the staggered point, no averaging)   */
 
 /* ---- source modes ------------------------------------------------------- */
 #define KWGB_ADDITIVE_MASS 0  /* mass source M of Eq. 4d, see kwgb_add_source  */
+#define KWGB_FORCE_X 1        /* force density along x, see kwgb_add_source    */
+#define KWGB_FORCE_Y 2
+#define KWGB_FORCE_Z 3
 
 /* ---- objectives of kwgb_adjoint ----------------------------------------- */
 #define KWGB_OBJ_MEAN_ABS_P 0  /* J = 1/(n_obj Nt) sum_{n=1..Nt} sum_i |p^n(idx_i)| */
@@ -144,30 +152,54 @@ int kwgb_set_initial_pressure(kwgb_sim* sim, const float* p0);
  * every split density gets rho_xi += dt * 2 s / (3 c0 dx), so a planar source
  * radiates a plane wave of amplitude s.  Points may repeat and sources may
  * overlap (contributions add).  Before the first step only.
- * *source_id receives the source number.  Errors: ARG, STATE, OOM, CUDA. */
+ * mode KWGB_FORCE_X / _Y / _Z instead adds a force density F [N/m^3] along
+ * that axis (the paper's velocity-updating source kind, Sec. 3.4): after the
+ * velocity update of Eq. 4b, u_xi += dt F / rho0_sg at the staggered point of
+ * each index, sample n at t = n dt; a planar force layer radiates pressure
+ * +-F dxi/2 on its two sides.
+ * *source_id receives the source number.  Errors: ARG (bad mode, sizes,
+ * indices), STATE, OOM, CUDA. */
 int kwgb_add_source(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
                     const float* signal, int64_t n_signals, int64_t n_t,
                     int mode, int32_t* source_id);
 
 /* Sensor at n_idx linear indices idx (host int64), or at every grid point
  * when idx is NULL (then n_idx is ignored).  record is a set of KWGB_P_MAX,
- * KWGB_P_RMS, KWGB_I_AVG.  Samples are p^1 .. p^Nt.  Before the first step
- * only.  *sensor_id receives the sensor number.  Errors: ARG, STATE, OOM. */
+ * KWGB_P_RMS, KWGB_I_AVG, KWGB_P_MIN, KWGB_P_SERIES, KWGB_U_SERIES (the
+ * aggregate and time-varying outputs collected at the sensor mask, Sec. 3.4).
+ * Samples are p^1 .. p^Nt and u^{1/2} .. u^{Nt-1/2}.  Before the first step
+ * only.  A sensor with a series needs kwgb_set_series_capacity before the
+ * first step.  *sensor_id receives the sensor number.  Errors: ARG, STATE,
+ * OOM. */
 int kwgb_add_sensor(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
                     uint32_t record, int32_t* sensor_id);
+
+/* Length n_t > 0 of the device ring buffer of a series sensor: it keeps the
+ * samples of the last n_t steps (n_t >= the run's steps keeps them all).
+ * Device memory: 4 n_t n_idx bytes for KWGB_P_SERIES, 12 n_t n_idx for
+ * KWGB_U_SERIES.  Before the first step only.  Errors: ARG, STATE. */
+int kwgb_set_series_capacity(kwgb_sim* sim, int32_t sensor_id, int64_t n_t);
 
 /* Advance n_steps time steps, (u^{n-1/2}, rho^n, p^n) -> (u^{n+1/2},
  * rho^{n+1}, p^{n+1}) per step, asynchronously on cuda_stream (a
  * cudaStream_t; NULL = the legacy default stream).  n_steps == 0 is a no-op.
- * Errors: ARG (n_steps < 0), STATE (no medium), CUDA. */
+ * The first step of a simulation launches its kernels directly and the
+ * library then captures one step into a CUDA graph (on a stream of its own)
+ * that later steps replay on cuda_stream; if capture is not possible the
+ * kernels keep being launched directly.  Either way the results are the
+ * same.  Errors: ARG (n_steps < 0), STATE (no medium), CUDA. */
 int kwgb_step(kwgb_sim* sim, int64_t n_steps, void* cuda_stream);
 
 /* Copy one sensor output to host_out as float64.  which is ONE of
- * KWGB_P_MAX (n_idx values), KWGB_P_RMS (n_idx values) or KWGB_I_AVG
- * (3*n_idx values: all x components, then y, then z).  n is the capacity of
+ * KWGB_P_MAX, KWGB_P_MIN, KWGB_P_RMS (n_idx values each), KWGB_I_AVG
+ * (3*n_idx values: all x components, then y, then z), KWGB_P_SERIES
+ * (m*n_idx values, [sample][point]) or KWGB_U_SERIES (m*3*n_idx values,
+ * [sample][component][point]), where m = min(steps taken, capacity) and the
+ * series hold the last m samples, oldest first.  n is the capacity of
  * host_out in doubles.  Synchronises.  The intensity's last term needs
  * u^{Nt+1/2}; it is computed here by one extra velocity update that changes
- * no state.  With no step taken p_max = -inf, p_rms = 0, I = 0.
+ * no state.  With no step taken p_max = -inf, p_min = +inf, p_rms = 0,
+ * I = 0 and the series are empty.
  * Errors: ARG (bad id/which, n too small, output not recorded), CUDA,
  * NONFINITE (pressure went non-finite; the values are still copied). */
 int kwgb_read(kwgb_sim* sim, int32_t sensor_id, uint32_t which,

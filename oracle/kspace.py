@@ -58,6 +58,12 @@ the same readings, written independently):
      the p series holds p^1 .. p^Nt at the sensor points, the u series
      u_xi^{1/2} .. u_xi^{Nt-1/2} (the value at the staggered point i + 1/2
      as stored, no averaging), both ordered [n][point] and [n][xi][point].
+ R15 Force sources (the paper's velocity-updating source kind, Sec. 3.4;
+     scaling not given): an additive force density F_xi [N/m^3] at the
+     mask points, u_xi^{n+1/2} += dt F_xi^n / rho0_sg after the update of
+     Eq. 4b (PML included), F^n = the caller's sample n (t = n dt, the time
+     level of the right-hand side of Eq. 4b); 0 after the signal ends.  A
+     planar force layer radiates pressure +-F dz/2 on its two sides.
 """
 
 import os
@@ -76,6 +82,7 @@ P_SERIES = 16
 U_SERIES = 32
 
 ADDITIVE_MASS = 0
+FORCE_X, FORCE_Y, FORCE_Z = 1, 2, 3
 
 OP_GRAD_FWD = 0   # Eq. 4a operator: i k_xi kappa exp(+i k_xi dxi / 2)
 OP_DIV_BWD = 1    # Eq. 4c operator: i k_xi kappa exp(-i k_xi dxi / 2)
@@ -224,6 +231,7 @@ class Simulation:
         self.rho = [np.zeros(shape) for _ in range(3)]
         self.n = 0
         self.sources = []
+        self.forces = []
         self.sensors = []
         self.medium_set = False
         self._build_operators()
@@ -271,16 +279,20 @@ class Simulation:
                   for i in range(3)]
 
     def add_source(self, idx, signal, mode=ADDITIVE_MASS):
-        """Additive mass source at linear indices idx; signal has shape
-        (n_t,) (shared) or (len(idx), n_t) (per point).  Reading R10."""
-        if mode != ADDITIVE_MASS:
-            raise ValueError("only additive mass sources")
+        """Additive mass source (reading R10) or force source along x, y or z
+        (FORCE_X/Y/Z, reading R15) at linear indices idx; signal has shape
+        (n_t,) (shared) or (len(idx), n_t) (per point)."""
+        if mode not in (ADDITIVE_MASS, FORCE_X, FORCE_Y, FORCE_Z):
+            raise ValueError("unknown source mode")
         idx = np.asarray(idx, dtype=np.int64)
         sig = np.asarray(signal, dtype=np.float64)
         if sig.ndim == 1:
             sig = np.broadcast_to(sig, (len(idx), sig.shape[0]))
-        self.sources.append((idx, sig))
-        return len(self.sources) - 1
+        if mode == ADDITIVE_MASS:
+            self.sources.append((idx, sig))
+        else:
+            self.forces.append((idx, sig, mode - 1))
+        return len(self.sources) + len(self.forces) - 1
 
     def add_sensor(self, idx=None, record=P_MAX):
         """Sensor at linear indices idx (None = every grid point)."""
@@ -305,14 +317,19 @@ class Simulation:
                 np.add.at(add, idx, self.g.dt * 2.0 * s / (3.0 * c0[idx] * dx))
         return add.reshape(self.g.shape)
 
-    def _velocity_update(self, p):
-        """Eq. 4a then Eq. 4b with the PML of reading R7; returns new u."""
+    def _velocity_update(self, p, n):
+        """Eq. 4a then Eq. 4b with the PML of reading R7 and the force sources
+        of step n (reading R15); returns new u."""
         P = _ft(p)
         out = []
         for i in range(3):
             g = _ift_real(self.Df[i] * P)                                            # Eq. 4a
             out.append(self.f_sg[i] * (self.f_sg[i] * self.u[i]
                                        - self.g.dt * g / self.rho0_sg[i]))           # Eq. 4b
+        for idx, sig, ax in self.forces:
+            if n < sig.shape[1]:
+                flat = out[ax].reshape(-1)
+                np.add.at(flat, idx, self.g.dt * sig[:, n] / self.rho0_sg[ax].reshape(-1)[idx])
         return out
 
     def _accumulate_intensity(self, p, u_old, u_new):
@@ -330,7 +347,7 @@ class Simulation:
         g = self.g
         dt = g.dt
         for _ in range(int(nsteps)):
-            u_new = self._velocity_update(self.p)
+            u_new = self._velocity_update(self.p, self.n)
             if self.n >= 1:
                 self._accumulate_intensity(self.p, self.u, u_new)
             self.u = u_new
@@ -385,7 +402,7 @@ class Simulation:
             if nt == 0:
                 return np.zeros_like(s["I"])
             tail = np.zeros_like(s["I"])
-            u_tail = self._velocity_update(self.p)   # u^{Nt+1/2}, not stored (R12)
+            u_tail = self._velocity_update(self.p, self.n)   # u^{Nt+1/2}, not stored (R12)
             pf = self.p.reshape(-1)[s["idx"]]
             for i, ax in enumerate((2, 1, 0)):
                 ubar_old = 0.5 * (np.roll(self.u[i], 1, axis=ax) + self.u[i])

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkwgb.so")
 
-SOURCES = ["yz_f32.cu", "yz_bf16.cu", "yz_f16.cu", "kernels_yz.cu", "kernels_x.cu", "kernels_misc.cu",
+SOURCES = ["yz_f32.cu", "yz_bf16.cu", "yz_f16.cu", "kernels_yz.cu", "kernels_x.cu", "kernels_xvel.cu", "kernels_misc.cu",
            "kernels_adj.cu", "capi.cu", "kwgb_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

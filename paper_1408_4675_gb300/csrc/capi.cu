@@ -33,6 +33,7 @@ struct HostSource {
     std::vector<int64_t> idx;
     std::vector<float> sig;
     int64_t nsig, nt;
+    int mode = KWGB_ADDITIVE_MASS;
 };
 
 struct HostSensor {
@@ -43,6 +44,9 @@ struct HostSensor {
     int64_t slot0;              // first slot (masked)
     int full_k;                 // index into the full-grid arrays
     int64_t i0;                 // first entry in the intensity list (-1: none)
+    int64_t cap = 0;            // series ring length (kwgb_set_series_capacity)
+    int64_t pser0 = -1;         // p series: offset of its ring in the p series buffer
+    int64_t user0 = -1;         // u series: offset of its ring in the u series buffer
 };
 
 thread_local std::string g_create_error;
@@ -80,7 +84,9 @@ struct kwgb_sim {
 
     std::vector<HostSource> hsrc;
     std::vector<HostSensor> hsens;
-    SourceC src{};
+    SourceC src{};              // additive mass sources
+    SourceC fsrc[3] = {};       // force sources along x, y, z
+    bool any_force = false;
     SensorC sens{};
     int64_t n_slots = 0;
     int64_t n_i = 0;            // intensity points
@@ -89,6 +95,12 @@ struct kwgb_sim {
     double* I = nullptr;
     double* I_tail = nullptr;
     float* ubuf = nullptr;
+    int64_t series_elems = 0;   // p series buffer (floats)
+    int64_t n_u = 0;            // points recording a u series
+    int64_t* u_idx = nullptr;
+    SeriesSlot* u_q = nullptr;
+    float* useries = nullptr;
+    int64_t useries_elems = 0;
     cudaStream_t last_stream = nullptr;
     int64_t launches = 0;       // kernels launched so far
     bool adjoint_done = false;
@@ -206,6 +218,7 @@ extern "C" int kwgb_create(const kwgb_grid_desc* desc, kwgb_sim** out) {
     sim->N = n[0] * n[1] * n[2];
     g.scale = (float)(1.0 / (double)sim->N);
     g.hk = (float)(desc->c_ref * desc->dt / 2.0);
+    g.hk2 = (float)((desc->c_ref * desc->dt / 2.0) * (desc->c_ref * desc->dt / 2.0));
     const double y = desc->alpha_power;
     double kmax2 = 0;
     for (int a = 0; a < 3; ++a) kmax2 += (kPi / dd[a]) * (kPi / dd[a]);
@@ -354,9 +367,10 @@ extern "C" int kwgb_set_medium(kwgb_sim* sim, const float* c0, const float* rho0
 
 static const char* const kKernelNames[] = {
     "y_fwd_p", "z_grad", "y_inv_grad", "x_vel", "y_fwd_u", "z_div", "y_inv_div", "x_dens",
-    "y_fwd_abs", "z_abs", "y_inv_abs", "x_eos", "intensity_gather", "intensity_accum", "advance_step"};
+    "y_fwd_abs", "z_abs", "y_inv_abs", "x_eos", "intensity_gather", "intensity_accum", "advance_step",
+    "series"};
 enum { K_Y_FWD_P, K_Z_GRAD, K_Y_INV_GRAD, K_X_VEL, K_Y_FWD_U, K_Z_DIV, K_Y_INV_DIV, K_X_DENS,
-       K_Y_FWD_ABS, K_Z_ABS, K_Y_INV_ABS, K_X_EOS, K_I_GATHER, K_I_ACCUM, K_ADVANCE, K_COUNT };
+       K_Y_FWD_ABS, K_Z_ABS, K_Y_INV_ABS, K_X_EOS, K_I_GATHER, K_I_ACCUM, K_ADVANCE, K_SERIES, K_COUNT };
 
 // Count a launch; when profiling, record an event after it on the launch stream.
 static int mark(kwgb_sim* sim, int kind, cudaStream_t s) {
@@ -426,7 +440,8 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
     if (sim->n_i) LKM(launch_intensity_gather(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, s), K_I_GATHER);
     // Eq. 4b (+ x R2C of u), Eq. 4c (y fwd, z fwd + operator + z inv, y inv)
     XVelArgs va{};
-    for (int a = 0; a < 3; ++a) { va.G[a] = sp[a]; va.u[a] = sim->u[a]; va.U[a] = sp[a]; }
+    for (int a = 0; a < 3; ++a) { va.G[a] = sp[a]; va.u[a] = sim->u[a]; va.U[a] = sp[a]; va.f[a] = sim->fsrc[a]; }
+    va.step = sim->d_step;
     LKM(launch_x_vel(g, sim->md, XV_STEP, va, s), K_X_VEL);
     if (sim->n_i)
         LKM(launch_intensity_accum(sim->n_i, sim->i_idx, g, sim->u, g.nx, sim->ubuf, sim->sens.p_sens,
@@ -453,6 +468,12 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
     } else {
         da.P = sim->P;
         LKM(launch_x_dens(g, sim->md, sim->src, sens, st, da, s), K_X_DENS);
+    }
+    if (sim->n_u || sim->sens.p_min || sim->sens.ser) {
+        const SensorC& sc = sim->sens;
+        const int64_t np = (sc.p_min || sc.ser) ? sim->n_slots : 0;
+        LKM(launch_series(np, sc.p_sens, sc.p_min, sc.ser, sc.series, sim->n_u, sim->u_idx, sim->u_q, sim->u,
+                          sim->useries, sim->d_step, s), K_SERIES);
     }
     LKM(launch_advance_step(sim->d_step, s), K_ADVANCE);
     return KWGB_OK;
@@ -542,7 +563,8 @@ extern "C" int kwgb_add_source(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
                                int mode, int32_t* source_id) {
     if (!sim) return KWGB_ERR_ARG;
     if (sim->frozen || sim->steps > 0) return fail(sim, KWGB_ERR_STATE, "sources must be added before stepping");
-    if (mode != KWGB_ADDITIVE_MASS) return fail(sim, KWGB_ERR_UNSUPPORTED, "only additive mass sources");
+    if (mode != KWGB_ADDITIVE_MASS && mode != KWGB_FORCE_X && mode != KWGB_FORCE_Y && mode != KWGB_FORCE_Z)
+        return fail(sim, KWGB_ERR_ARG, "unknown source mode");
     if (n_idx < 0 || n_t < 0) return fail(sim, KWGB_ERR_ARG, "negative size");
     if (n_idx > 0 && (!idx || (n_t > 0 && !signal))) return fail(sim, KWGB_ERR_ARG, "null idx or signal");
     if (!(n_signals == 1 || n_signals == n_idx)) return fail(sim, KWGB_ERR_ARG, "n_signals must be 1 or n_idx");
@@ -552,6 +574,7 @@ extern "C" int kwgb_add_source(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
         if (v < 0 || v >= sim->N) return fail(sim, KWGB_ERR_ARG, "source index out of range");
     hs.nsig = n_signals;
     hs.nt = n_t;
+    hs.mode = mode;
     if (n_t > 0 && n_idx > 0) hs.sig.assign(signal, signal + n_signals * n_t);
     sim->hsrc.push_back(std::move(hs));
     if (source_id) *source_id = (int32_t)sim->hsrc.size() - 1;
@@ -562,16 +585,16 @@ extern "C" int kwgb_add_sensor(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
                                uint32_t record, int32_t* sensor_id) {
     if (!sim) return KWGB_ERR_ARG;
     if (sim->frozen || sim->steps > 0) return fail(sim, KWGB_ERR_STATE, "sensors must be added before stepping");
-    if (record == 0 || (record & ~(KWGB_P_MAX | KWGB_P_RMS | KWGB_I_AVG)))
-        return fail(sim, KWGB_ERR_ARG, "bad record flags");
+    const uint32_t all = KWGB_P_MAX | KWGB_P_RMS | KWGB_I_AVG | KWGB_P_MIN | KWGB_P_SERIES | KWGB_U_SERIES;
+    if (record == 0 || (record & ~all)) return fail(sim, KWGB_ERR_ARG, "bad record flags");
     HostSensor hs{};
     hs.record = record;
     hs.i0 = -1;
     if (idx == nullptr) {
         int nfull = 0;
         for (auto& o : sim->hsens) nfull += o.full ? 1 : 0;
-        if ((record & KWGB_I_AVG) || nfull >= 4) {
-            // full-grid intensity (or a fifth full-grid sensor): list every point
+        if ((record & (KWGB_I_AVG | KWGB_P_SERIES | KWGB_U_SERIES)) || nfull >= 4) {
+            // full-grid intensity or series (or a fifth full-grid sensor): list every point
             hs.full = false;
             hs.idx.resize(sim->N);
             std::iota(hs.idx.begin(), hs.idx.end(), int64_t(0));
@@ -592,16 +615,28 @@ extern "C" int kwgb_add_sensor(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
     return KWGB_OK;
 }
 
-// Build the device source/sensor structures (once, at the first step).
-static int freeze(kwgb_sim* sim) {
-    if (sim->frozen) return KWGB_OK;
+extern "C" int kwgb_set_series_capacity(kwgb_sim* sim, int32_t sensor_id, int64_t n_t) {
+    if (!sim) return KWGB_ERR_ARG;
+    if (sim->frozen || sim->steps > 0) return fail(sim, KWGB_ERR_STATE, "series capacity must be set before stepping");
+    if (sensor_id < 0 || sensor_id >= (int32_t)sim->hsens.size()) return fail(sim, KWGB_ERR_ARG, "bad sensor id");
+    if (n_t <= 0 || n_t > INT32_MAX) return fail(sim, KWGB_ERR_ARG, "capacity must be in [1, 2^31)");
+    HostSensor& h = sim->hsens[sensor_id];
+    if (!(h.record & (KWGB_P_SERIES | KWGB_U_SERIES))) return fail(sim, KWGB_ERR_ARG, "sensor records no series");
+    h.cap = n_t;
+    return KWGB_OK;
+}
+
+// Row-CSR device lists of the sources of one kind (unique points per grid
+// row, each with its contributions: signal offset, length and scale sc).
+static int build_sources(kwgb_sim* sim, int mode, float sc, SourceC* out) {
+    *out = SourceC{};
     const int64_t nx = sim->g.nx;
     const int64_t nrows = (int64_t)sim->g.ny * sim->g.nz;
-    // ---- sources: contributions sorted by grid index, unique points per row
     struct Contrib { int64_t L; int64_t off; int32_t nt; };
     std::vector<Contrib> cs;
     std::vector<float> sig;
     for (auto& s : sim->hsrc) {
+        if (s.mode != mode) continue;
         const int64_t base = (int64_t)sig.size();
         sig.insert(sig.end(), s.sig.begin(), s.sig.end());
         for (size_t i = 0; i < s.idx.size(); ++i)
@@ -613,8 +648,6 @@ static int freeze(kwgb_sim* sim) {
         std::vector<int64_t> c_off;
         std::vector<int32_t> c_nt;
         std::vector<float> c_scale;
-        // dt M_xi = dt * 2 s / (3 c0 dx); the kernel divides by c0
-        const float sc = (float)(sim->d.dt * 2.0 / (3.0 * sim->d.dx));
         for (size_t i = 0; i < cs.size(); ++i) {
             if (i == 0 || cs[i].L != cs[i - 1].L) {
                 pt_x.push_back((int32_t)(cs[i].L % nx));
@@ -638,7 +671,23 @@ static int freeze(kwgb_sim* sim) {
         if (int e = upload(sim, &d_cs, c_scale)) return e;
         if (sig.empty()) sig.push_back(0.f);
         if (int e = upload(sim, &d_sig, sig)) return e;
-        sim->src = SourceC{d_rp, d_px, d_pc, d_coff, d_cnt, d_cs, d_sig};
+        *out = SourceC{d_rp, d_px, d_pc, d_coff, d_cnt, d_cs, d_sig};
+    }
+    return KWGB_OK;
+}
+
+// Build the device source/sensor structures (once, at the first step).
+static int freeze(kwgb_sim* sim) {
+    if (sim->frozen) return KWGB_OK;
+    const int64_t nx = sim->g.nx;
+    const int64_t nrows = (int64_t)sim->g.ny * sim->g.nz;
+    // ---- sources: per kind, contributions sorted by grid index, unique points per row
+    // mass: dt M_xi = dt * 2 s / (3 c0 dx), the kernel divides by c0;
+    // force along xi: dt F / rho0_sg, the kernel divides by rho0_sg
+    if (int e = build_sources(sim, KWGB_ADDITIVE_MASS, (float)(sim->d.dt * 2.0 / (3.0 * sim->d.dx)), &sim->src)) return e;
+    for (int a = 0; a < 3; ++a) {
+        if (int e = build_sources(sim, KWGB_FORCE_X + a, (float)sim->d.dt, &sim->fsrc[a])) return e;
+        sim->any_force |= sim->fsrc[a].row_ptr != nullptr;
     }
     // ---- sensors
     SensorC& sc = sim->sens;
@@ -655,6 +704,10 @@ static int freeze(kwgb_sim* sim) {
             DALLOC(sc.full_p2[sc.nfull], double, sim->N);
             LK(launch_fill_f32(sc.full_max[sc.nfull], sim->N, -INFINITY, nullptr));
             CK(cudaMemset(sc.full_p2[sc.nfull], 0, sim->N * sizeof(double)));
+            if (h.record & KWGB_P_MIN) {
+                DALLOC(sc.full_min[sc.nfull], float, sim->N);
+                LK(launch_fill_f32(sc.full_min[sc.nfull], sim->N, INFINITY, nullptr));
+            }
             sc.nfull++;
             continue;
         }
@@ -689,6 +742,52 @@ static int freeze(kwgb_sim* sim) {
         LK(launch_fill_f32(sc.p_max, slots, -INFINITY, nullptr));
         CK(cudaMemset(sc.p2, 0, slots * sizeof(double)));
         CK(cudaMemset(sc.p_sens, 0, slots * sizeof(float)));
+        // p_min and the series rings (time-varying outputs at the sensor mask, Sec. 3.4)
+        bool any_min = false, any_pser = false;
+        std::vector<SeriesSlot> ser(slots, SeriesSlot{-1, 0, 1});
+        std::vector<int64_t> uidx;
+        std::vector<SeriesSlot> uq;
+        int64_t ptot = 0, utot = 0;
+        for (auto& h : sim->hsens) {
+            if (h.full) continue;
+            any_min |= (h.record & KWGB_P_MIN) != 0;
+            if ((h.record & (KWGB_P_SERIES | KWGB_U_SERIES)) && h.cap <= 0)
+                return fail(sim, KWGB_ERR_ARG, "a series sensor needs kwgb_set_series_capacity before stepping");
+            if (h.record & KWGB_P_SERIES) {
+                any_pser = true;
+                h.pser0 = ptot;
+                for (int64_t i = 0; i < h.n; ++i) ser[h.slot0 + i] = SeriesSlot{ptot + i, (int32_t)h.n, (int32_t)h.cap};
+                ptot += h.cap * h.n;
+            }
+            if (h.record & KWGB_U_SERIES) {
+                h.user0 = utot;
+                for (int64_t i = 0; i < h.n; ++i) {
+                    uidx.push_back(h.idx[i]);
+                    uq.push_back(SeriesSlot{utot + i, (int32_t)h.n, (int32_t)h.cap});
+                }
+                utot += 3 * h.cap * h.n;
+            }
+        }
+        if (any_min) {
+            DALLOC(sc.p_min, float, slots);
+            LK(launch_fill_f32(sc.p_min, slots, INFINITY, nullptr));
+        }
+        if (any_pser) {
+            SeriesSlot* d_ser;
+            if (int e = upload(sim, &d_ser, ser)) return e;
+            sc.ser = d_ser;
+            DALLOC(sc.series, float, ptot);
+            CK(cudaMemset(sc.series, 0, ptot * sizeof(float)));
+            sim->series_elems = ptot;
+        }
+        if (!uidx.empty()) {
+            if (int e = upload(sim, &sim->u_idx, uidx)) return e;
+            if (int e = upload(sim, &sim->u_q, uq)) return e;
+            DALLOC(sim->useries, float, utot);
+            CK(cudaMemset(sim->useries, 0, utot * sizeof(float)));
+            sim->n_u = (int64_t)uidx.size();
+            sim->useries_elems = utot;
+        }
     }
     sim->n_i = (int64_t)ii.size();
     if (sim->n_i) {
@@ -741,12 +840,16 @@ static std::vector<std::pair<void*, size_t>> state_blocks(kwgb_sim* sim) {
         b.push_back({sc.p_max, sim->n_slots * sizeof(float)});
         b.push_back({sc.p2, sim->n_slots * sizeof(double)});
         b.push_back({sc.p_sens, sim->n_slots * sizeof(float)});
+        if (sc.p_min) b.push_back({sc.p_min, sim->n_slots * sizeof(float)});
     }
     for (int k = 0; k < sc.nfull; ++k) {
         b.push_back({sc.full_max[k], (size_t)sim->N * sizeof(float)});
         b.push_back({sc.full_p2[k], (size_t)sim->N * sizeof(double)});
+        if (sc.full_min[k]) b.push_back({sc.full_min[k], (size_t)sim->N * sizeof(float)});
     }
     if (sim->n_i) b.push_back({sim->I, 3 * sim->n_i * sizeof(double)});
+    if (sim->series_elems) b.push_back({sc.series, sim->series_elems * sizeof(float)});
+    if (sim->useries_elems) b.push_back({sim->useries, sim->useries_elems * sizeof(float)});
     return b;
 }
 
@@ -885,24 +988,40 @@ extern "C" int kwgb_read(kwgb_sim* sim, int32_t sensor_id, uint32_t which, doubl
     if (sensor_id < 0 || sensor_id >= (int32_t)sim->hsens.size()) return fail(sim, KWGB_ERR_ARG, "bad sensor id");
     if (!host_out) return fail(sim, KWGB_ERR_ARG, "null output");
     HostSensor& h = sim->hsens[sensor_id];
-    if (!(which == KWGB_P_MAX || which == KWGB_P_RMS || which == KWGB_I_AVG))
-        return fail(sim, KWGB_ERR_ARG, "which must be one of P_MAX, P_RMS, I_AVG");
+    if (!(which == KWGB_P_MAX || which == KWGB_P_RMS || which == KWGB_I_AVG || which == KWGB_P_MIN ||
+          which == KWGB_P_SERIES || which == KWGB_U_SERIES))
+        return fail(sim, KWGB_ERR_ARG, "which must be one of P_MAX, P_RMS, I_AVG, P_MIN, P_SERIES, U_SERIES");
     if (!(h.record & which)) return fail(sim, KWGB_ERR_ARG, "output not recorded by this sensor");
-    const int64_t need = which == KWGB_I_AVG ? 3 * h.n : h.n;
-    if (n < need) return fail(sim, KWGB_ERR_ARG, "output buffer too small");
     const int64_t nt = sim->steps;
+    const int64_t m = (nt == 0 || !sim->frozen) ? 0 : std::min<int64_t>(nt, h.cap);   // series samples kept
+    const int64_t need = which == KWGB_I_AVG ? 3 * h.n
+                       : which == KWGB_P_SERIES ? m * h.n
+                       : which == KWGB_U_SERIES ? 3 * m * h.n : h.n;
+    if (n < need) return fail(sim, KWGB_ERR_ARG, "output buffer too small");
     if (nt == 0 || !sim->frozen) {
-        for (int64_t i = 0; i < need; ++i) host_out[i] = which == KWGB_P_MAX ? -INFINITY : 0.0;
+        const double v = which == KWGB_P_MAX ? -INFINITY : (which == KWGB_P_MIN ? INFINITY : 0.0);
+        for (int64_t i = 0; i < need; ++i) host_out[i] = v;
         return KWGB_OK;
     }
     int status = sync_and_flag(sim);
     if (status == KWGB_ERR_CUDA) return status;
     const SensorC& sc = sim->sens;
-    if (which == KWGB_P_MAX) {
+    if (which == KWGB_P_MAX || which == KWGB_P_MIN) {
         std::vector<float> t(h.n);
-        const float* src = h.full ? sc.full_max[h.full_k] : sc.p_max + h.slot0;
+        const float* src = which == KWGB_P_MAX ? (h.full ? sc.full_max[h.full_k] : sc.p_max + h.slot0)
+                                               : (h.full ? sc.full_min[h.full_k] : sc.p_min + h.slot0);
         CK(cudaMemcpy(t.data(), src, h.n * sizeof(float), cudaMemcpyDeviceToHost));
         for (int64_t i = 0; i < h.n; ++i) host_out[i] = t[i];
+    } else if (which == KWGB_P_SERIES || which == KWGB_U_SERIES) {
+        // ring row of sample t is t mod cap; the last m samples, oldest first
+        const int64_t w = which == KWGB_P_SERIES ? h.n : 3 * h.n;
+        const float* src = which == KWGB_P_SERIES ? sc.series + h.pser0 : sim->useries + h.user0;
+        std::vector<float> t((size_t)h.cap * w);
+        CK(cudaMemcpy(t.data(), src, t.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        for (int64_t r = 0; r < m; ++r) {
+            const int64_t row = (nt - m + r) % h.cap;
+            for (int64_t i = 0; i < w; ++i) host_out[r * w + i] = t[row * w + i];
+        }
     } else if (which == KWGB_P_RMS) {
         const double* src = h.full ? sc.full_p2[h.full_k] : sc.p2 + h.slot0;
         CK(cudaMemcpy(host_out, src, h.n * sizeof(double), cudaMemcpyDeviceToHost));
@@ -920,7 +1039,9 @@ extern "C" int kwgb_read(kwgb_sim* sim, int32_t sensor_id, uint32_t which, doubl
         LK(zop(sim, Z_GRAD_FWD, zin, out, s));
         LK(ypass(sim, +1, out, out, 3, s));
         XVelArgs va{};
+        va.step = sim->d_step;
         for (int a = 0; a < 3; ++a) {
+            va.f[a] = sim->fsrc[a];
             va.G[a] = out[a];
             va.u[a] = sim->u[a];
             va.tail[a] = reinterpret_cast<float*>(out[a]);
@@ -1042,6 +1163,9 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
     if (sim->steps != 0 || sim->frozen || sim->adjoint_done)
         return fail(sim, KWGB_ERR_STATE, "kwgb_adjoint needs a simulation that has not stepped");
     if (objective != KWGB_OBJ_MEAN_ABS_P) return fail(sim, KWGB_ERR_ARG, "unknown objective");
+    for (auto& h : sim->hsrc)
+        if (h.mode != KWGB_ADDITIVE_MASS)
+            return fail(sim, KWGB_ERR_UNSUPPORTED, "the adjoint differentiates additive mass sources only");
     if (!obj_idx || n_obj <= 0 || n_steps <= 0 || checkpoint_every <= 0 || !J_out)
         return fail(sim, KWGB_ERR_ARG, "bad objective, step count or checkpoint interval");
     {
@@ -1145,12 +1269,16 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
         sarr.push_back({sc_.p_max, sim->n_slots * sizeof(float)});
         sarr.push_back({sc_.p2, sim->n_slots * sizeof(double)});
         sarr.push_back({sc_.p_sens, sim->n_slots * sizeof(float)});
+        if (sc_.p_min) sarr.push_back({sc_.p_min, sim->n_slots * sizeof(float)});
     }
     for (int k = 0; k < sc_.nfull; ++k) {
         sarr.push_back({sc_.full_max[k], N * sizeof(float)});
         sarr.push_back({sc_.full_p2[k], N * sizeof(double)});
+        if (sc_.full_min[k]) sarr.push_back({sc_.full_min[k], N * sizeof(float)});
     }
     if (sim->n_i) sarr.push_back({sim->I, 3 * sim->n_i * sizeof(double)});
+    if (sim->series_elems) sarr.push_back({sc_.series, sim->series_elems * sizeof(float)});
+    if (sim->useries_elems) sarr.push_back({sim->useries, sim->useries_elems * sizeof(float)});
     size_t sbytes = 0;
     for (auto& a : sarr) sbytes += a.second;
     char* snap = static_cast<char*>(dalloc(sim, std::max<size_t>(sbytes, 16)));

@@ -47,6 +47,45 @@ cudaError_t launch_init_rho(const GridC& g, const Medium& m, const float* p0, in
 
 __global__ void advance_step_kernel(int64_t* step) { *step += 1; }
 
+// Per-step work of the p_min / series sensors, after the pressure pass (which
+// leaves p^{n+1} of every masked sensor slot in p_sens): slots k < n_slots
+// update p_min and write sample n of their p series; points k < n_u write
+// u_xi^{n+1/2} into their u series.
+__global__ void series_kernel(int64_t n_slots, const float* __restrict__ p_sens, float* p_min,
+                              const SeriesSlot* __restrict__ ser, float* series, int64_t n_u,
+                              const int64_t* __restrict__ idx, const SeriesSlot* __restrict__ uq,
+                              const float* __restrict__ ux, const float* __restrict__ uy,
+                              const float* __restrict__ uz, float* useries, const int64_t* __restrict__ step) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = *step;
+    if (k < n_slots) {
+        const float v = p_sens[k];
+        if (p_min) p_min[k] = fminf(p_min[k], v);
+        if (ser) {
+            const SeriesSlot q = ser[k];
+            if (q.base >= 0) series[q.base + (n % q.cap) * q.stride] = v;
+        }
+    }
+    if (k < n_u) {
+        const SeriesSlot q = uq[k];
+        const int64_t L = idx[k];
+        const int64_t o = q.base + (n % q.cap) * 3 * (int64_t)q.stride;
+        useries[o] = ux[L];
+        useries[o + q.stride] = uy[L];
+        useries[o + 2 * (int64_t)q.stride] = uz[L];
+    }
+}
+
+cudaError_t launch_series(int64_t n_slots, const float* p_sens, float* p_min, const SeriesSlot* ser, float* series,
+                          int64_t n_u, const int64_t* idx, const SeriesSlot* uq, float* const* u, float* useries,
+                          const int64_t* step, cudaStream_t s) {
+    const int64_t n = n_slots > n_u ? n_slots : n_u;
+    if (n <= 0) return cudaSuccess;
+    series_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_slots, p_sens, p_min, ser, series, n_u, idx, uq,
+                                                               u[0], u[1], u[2], useries, step);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_advance_step(int64_t* step, cudaStream_t s) {
     advance_step_kernel<<<1, 1, 0, s>>>(step);
     return cudaGetLastError();

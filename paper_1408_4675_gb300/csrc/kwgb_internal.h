@@ -35,6 +35,7 @@ struct GridC {
     float dt;
     float scale;              // 1 / (nx ny nz): inverse-FFT normalisation
     float hk;                 // c_ref dt / 2, argument factor of kappa
+    float hk2;                // hk^2 (kappa is evaluated from (hk k)^2)
     float inv_kmax2;          // 1 / max k^2
     float abs_e[2];           // (y-2)/2, (y-1)/2: powers of k^2 / kmax^2 in Eq. 8
     float abs_c[2];           // kmax^(y-2), kmax^(y-1)
@@ -76,6 +77,14 @@ struct SourceC {
 };
 
 // Masked sensor points (CSR over rows) and full-grid sensors.
+// Where the samples of one sensor point go in a series ring buffer:
+// sample n at base + (n mod cap) * stride (u series: base + ((n mod cap) * 3 + xi) * stride).
+struct SeriesSlot {
+    int64_t base;             // < 0: the point records no series
+    int32_t stride;           // points of its sensor
+    int32_t cap;              // ring length
+};
+
 struct SensorC {
     const int32_t* row_ptr;   // nrows + 1, NULL when no masked sensor points
     const int32_t* e_x;       // x of each entry
@@ -83,9 +92,13 @@ struct SensorC {
     float* p_max;             // per slot
     double* p2;               // per slot, sum of p^2
     float* p_sens;            // per slot, last p (intensity)
+    float* p_min;             // per slot (NULL when no sensor records P_MIN); updated by launch_series
+    const SeriesSlot* ser;    // per slot (NULL when no sensor records a p series)
+    float* series;            // p series ring buffers
     int nfull;                // full-grid sensors (<= 4)
     float* full_max[4];
     double* full_p2[4];
+    float* full_min[4];       // NULL unless that sensor records P_MIN
 };
 
 struct StepC {
@@ -114,6 +127,8 @@ struct XVelArgs {
     float* u[3];              // velocity (pitch nx)
     float2* U[3];             // XV_STEP: x-R2C of the new velocity (may alias G)
     float* tail[3];           // XV_TAIL: u^{Nt+1/2} written as real rows of pitch 2*nhp
+    SourceC f[3];             // force sources along x, y, z (row_ptr NULL: none)
+    const int64_t* step;      // device step counter (force samples)
 };
 cudaError_t launch_x_vel(const GridC& g, const Medium& m, int mode, const XVelArgs& a,
                          cudaStream_t s);
@@ -149,6 +164,10 @@ cudaError_t launch_x_c2r(const GridC& g, const float2* in, float* out, int out_p
 cudaError_t launch_init_rho(const GridC& g, const Medium& m, const float* p0, int p0_pitch,
                             float* rho[3], cudaStream_t s);
 cudaError_t launch_advance_step(int64_t* step, cudaStream_t s);
+// p_min and series sensors of one step: masked slots (p from p_sens) and u-series points
+cudaError_t launch_series(int64_t n_slots, const float* p_sens, float* p_min, const SeriesSlot* ser, float* series,
+                          int64_t n_u, const int64_t* idx, const SeriesSlot* uq, float* const* u, float* useries,
+                          const int64_t* step, cudaStream_t s);
 cudaError_t launch_intensity_gather(int64_t n, const int64_t* idx, const GridC& g,
                                     float* const* u, int pitch, float* ubuf, cudaStream_t s);
 cudaError_t launch_intensity_accum(int64_t n, const int64_t* idx, const GridC& g,

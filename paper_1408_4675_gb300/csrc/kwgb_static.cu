@@ -128,6 +128,7 @@ extern "C" int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const fl
     g.dt = (float)desc->dt;
     g.scale = (float)(1.0 / ((double)g.nx * g.ny * g.nz));
     g.hk = (float)(desc->c_ref * desc->dt / 2.0);
+    g.hk2 = (float)((desc->c_ref * desc->dt / 2.0) * (desc->c_ref * desc->dt / 2.0));
     g.num_sms = sms;
 
     // tables, built here in float64 and copied into the scratch (fixed-size host arrays)

@@ -76,13 +76,15 @@ struct alignas(64) YZK {
     int* flag;
 };
 
-// sinc(x) = sin(x)/x with sinc(0) = 1 (kappa of Sec. 2.2).  For |x| <= 3 the
-// Taylor series sum_n (-x^2)^n / (2n+1)! up to n = 9 is used (branch-free; the
-// truncation error is below the n = 10 term, 3^20/21! < 7e-11); beyond that
-// sin(x)/x directly.
-__device__ __forceinline__ float sinc_f(float x) {
-    const float x2 = x * x;
-    if (x2 > 9.0f) return __fdividef(sinf(x), x);
+// sinc(x) = sin(x)/x with sinc(0) = 1 (kappa of Sec. 2.2), as a function of
+// x^2 so that no square root is needed on the usual path: for x^2 <= 9 the
+// Taylor series sum_n (-x^2)^n / (2n+1)! up to n = 9 (truncation error below
+// the n = 10 term, 3^20/21! < 7e-11); beyond that sin(x)/x directly.
+__device__ __forceinline__ float sinc_sq(float x2) {
+    if (x2 > 9.0f) {
+        const float x = sqrtf(x2);
+        return __fdividef(sinf(x), x);
+    }
     float p = -1.0f / 121645100408832000.0f;          // -1/19!
     p = fmaf(p, x2, 1.0f / 355687428096000.0f);       //  1/17!
     p = fmaf(p, x2, -1.0f / 1307674368000.0f);        // -1/15!
@@ -217,7 +219,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                     const float kz = __ldg(g.t.kz + j + TL * m);
                     const float k2 = fmaf(kx, kx, fmaf(ky, ky, kz * kz));
                     if (OP == OP_Z_ABS) lg[m] = k2 > 0.f ? log2f(k2 * g.inv_kmax2) : -INFINITY;
-                    else kap[m] = sinc_f(g.hk * sqrtf(k2)) * g.scale;
+                    else kap[m] = sinc_sq(g.hk2 * k2) * g.scale;
                 }
             }
             if (!MIXED) line_fft<LOGN, E, -1>(v, j, S, g.t.tw);

@@ -20,8 +20,9 @@ ERRORS = {-1: "ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: 
           -7: "UNSUPPORTED"}
 
 NONLINEAR, ABSORBING = 1, 2
-P_MAX, P_RMS, I_AVG = 1, 2, 4
+P_MAX, P_RMS, I_AVG, P_MIN, P_SERIES, U_SERIES = 1, 2, 4, 8, 16, 32
 ADDITIVE_MASS = 0
+FORCE_X, FORCE_Y, FORCE_Z = 1, 2, 3
 SCALAR_C0, SCALAR_RHO0, SCALAR_BONA, SCALAR_ALPHA0 = 1, 2, 4, 8
 INPUT_DEVICE = 0x80000000
 FIELD_P, FIELD_UX, FIELD_UY, FIELD_UZ, FIELD_RHOX, FIELD_RHOY, FIELD_RHOZ = range(7)
@@ -84,6 +85,8 @@ def load():
     L.kwgb_kernel_name.restype = ctypes.c_char_p
     L.kwgb_adjoint.argtypes = [vp, vp, i64, ctypes.c_int, i64, i64, ctypes.POINTER(ctypes.c_double), vp, i64, vp]
     L.kwgb_adjoint.restype = ctypes.c_int
+    L.kwgb_set_series_capacity.argtypes = [vp, i32, i64]
+    L.kwgb_set_series_capacity.restype = ctypes.c_int
     L.kwgb_state_bytes.argtypes = [vp]
     L.kwgb_state_bytes.restype = i64
     L.kwgb_save_state.argtypes = [vp, vp, i64]
@@ -144,6 +147,7 @@ class Simulation:
         self.h = h
         self._cb = None
         self._sensors = []
+        self._caps = []
         self._src_shapes = []
         if use_torch_allocator:
             self._use_torch_allocator()
@@ -229,7 +233,13 @@ class Simulation:
             self._check(self.L.kwgb_add_sensor(self.h, _ptr(idx), idx.size, record, ctypes.byref(sid)))
             n = idx.size
         self._sensors.append(n)
+        self._caps.append(0)
         return sid.value
+
+    def set_series_capacity(self, sensor_id, n_t):
+        """Ring length of a P_SERIES / U_SERIES sensor (the last n_t steps are kept)."""
+        self._check(self.L.kwgb_set_series_capacity(self.h, sensor_id, int(n_t)))
+        self._caps[sensor_id] = int(n_t)
 
     # -- stepping and outputs -----------------------------------------------
     def step(self, n=1, stream=None):
@@ -256,10 +266,14 @@ class Simulation:
         self._check(self.L.kwgb_load_state(self.h, _ptr(buf), buf.size))
 
     def read(self, sensor_id, which):
-        n = self._sensors[sensor_id] * (3 if which == I_AVG else 1)
-        out = np.empty(n, dtype=np.float64)
-        self._check(self.L.kwgb_read(self.h, sensor_id, which, _ptr(out), n))
-        return out.reshape(3, -1) if which == I_AVG else out
+        """P_MAX / P_MIN / P_RMS: (n,); I_AVG: (3, n); P_SERIES: (m, n); U_SERIES:
+        (m, 3, n) with m = min(steps taken, capacity), oldest sample first."""
+        npts = self._sensors[sensor_id]
+        m = min(self.steps_done, self._caps[sensor_id])
+        shape = {I_AVG: (3, npts), P_SERIES: (m, npts), U_SERIES: (m, 3, npts)}.get(which, (npts,))
+        out = np.empty(int(np.prod(shape)), dtype=np.float64)
+        self._check(self.L.kwgb_read(self.h, sensor_id, which, _ptr(out), out.size))
+        return out.reshape(shape)
 
     def read_field(self, name):
         out = np.empty(self.shape, dtype=np.float32)
@@ -329,7 +343,10 @@ def from_config(cfg, use_torch_allocator=True):
     sim.set_medium(cfg["c0"], cfg["rho0"], cfg["bona"], cfg["alpha0"])
     if cfg.get("p0") is not None:
         sim.set_initial_pressure(cfg["p0"])
-    for idx, sig in cfg["sources"]:
-        sim.add_source(idx, sig)
+    for src in cfg["sources"]:                     # (idx, signal) or (idx, signal, mode)
+        sim.add_source(*src)
     ids = [sim.add_sensor(idx, rec) for idx, rec in cfg["sensors"]]
+    for i, (idx, rec) in zip(ids, cfg["sensors"]):
+        if rec & (P_SERIES | U_SERIES):
+            sim.set_series_capacity(i, cfg.get("series_capacity", cfg["n_steps"]))
     return sim, ids

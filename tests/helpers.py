@@ -17,8 +17,8 @@ def oracle_from_config(cfg):
     sim.set_medium(f32(cfg["c0"]), f32(cfg["rho0"]), f32(cfg["bona"]), f32(cfg["alpha0"]))
     if cfg.get("p0") is not None:
         sim.set_initial_pressure(f32(cfg["p0"]))
-    for idx, sig in cfg["sources"]:
-        sim.add_source(idx, f32(sig))
+    for src in cfg["sources"]:                     # (idx, signal) or (idx, signal, mode)
+        sim.add_source(src[0], f32(src[1]), *src[2:])
     ids = [sim.add_sensor(idx, rec) for idx, rec in cfg["sensors"]]
     return sim, ids
 

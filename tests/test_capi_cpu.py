@@ -6,6 +6,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_1408_4675_gb300 import build, kwgb
@@ -99,3 +101,19 @@ def test_snapshot_calls_without_device(lib):
     assert lib.kwgb_save_state(None, buf, ctypes.c_int64(64)) == -1
     lib.kwgb_destroy(h)
 
+
+
+def test_series_capacity_validation_without_device():
+    sim = kwgb.Simulation((16, 16, 16), (1e-4,) * 3, 2e-8, 1500.0)
+    L = sim.L
+    sid = sim.add_sensor(np.array([1, 2, 3]), kwgb.P_SERIES)
+    other = sim.add_sensor(np.array([1]), kwgb.P_MAX)
+    assert L.kwgb_set_series_capacity(sim.h, sid, 0) == -1          # capacity must be >= 1
+    assert L.kwgb_set_series_capacity(sim.h, 99, 3) == -1           # bad sensor id
+    assert L.kwgb_set_series_capacity(sim.h, other, 3) == -1        # records no series
+    assert L.kwgb_set_series_capacity(sim.h, sid, 3) == 0
+    # outputs before any step: no device access needed
+    assert sim.read(sid, kwgb.P_SERIES).shape == (0, 3)
+    assert np.all(np.isneginf(sim.read(other, kwgb.P_MAX)))
+    assert L.kwgb_add_sensor(sim.h, None, 0, 64, ctypes.byref(ctypes.c_int32())) == -1   # unknown record bit
+    sim.close()

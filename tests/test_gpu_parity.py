@@ -230,3 +230,25 @@ def test_mixed_form_equal_error(kw, form, cfgid, n, steps):
                 print("%s cfg%d which %d rel_l2 %.3e linf %.3e" % (form, cfgid, which, rel_l2(got, ref), linf(got, ref)))
     _check_outputs(gsim, gids, osim, oids, cfg, tl2, tinf)
     gsim.close()
+
+
+def test_force_sources_match_oracle(kw):
+    """Force sources (reading R15): a planar z force layer with a shared
+    signal and x-force points with their own signals, in the heterogeneous
+    nonlinear absorbing medium, with intensity sensors (whose read-time tail
+    applies the next step's force samples)."""
+    steps = 50
+    cfg = inputs.make_config(2, n=32, n_steps=steps)
+    n = 32
+    yy, xx = np.meshgrid(np.arange(12, 20), np.arange(12, 20), indexing="ij")
+    plane = (xx + n * (yy + n * 11)).ravel()
+    pts = np.array([5 + n * (7 + n * 16), 20 + n * (9 + n * 18), 21 + n * (9 + n * 18)])
+    t = np.arange(steps) * cfg["dt"]
+    f1 = 5e10 * np.sin(2 * np.pi * 1e6 * t)
+    f2 = np.stack([4e10 * np.sin(2 * np.pi * 1e6 * t + k) for k in range(3)])
+    cfg["sources"] = cfg["sources"] + [(plane, f1, kw.FORCE_Z), (pts, f2[:, :30], kw.FORCE_X)]
+    cfg["sensors"] = [(np.sort(np.concatenate([plane[::7], pts])), 7), (None, 3)]
+    gsim, gids, osim, oids = _run_both(kw, cfg, steps)
+    _check_outputs(gsim, gids, osim, oids, cfg, 1e-3, 5e-3)
+    _check_fields(gsim, osim, 1e-3, 5e-3)
+    gsim.close()

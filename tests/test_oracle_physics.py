@@ -1,6 +1,6 @@
 """Physics pins of the FP64 oracle: the nonlinear coefficient beta = 1 + B/2A
 that Eq. 2 implies (Fubini's pre-shock harmonics of a plane wave), the
-emitted amplitude of the additive mass source, and a PML sanity check (the
+emitted amplitudes of the additive mass source and of the force source, and a PML sanity check (the
 paper gives no PML profile, so the PML itself stays unpinned)."""
 
 import math
@@ -109,3 +109,37 @@ def test_pml_reflection_below_minus_35_db():
     sim.step(int(2 * (nz / 2) / 0.3) + 40)
     interior = np.abs(sim.p[15:nz - 15, 1, 1]).max()
     assert 20 * math.log10(interior / 0.5) < -35.0, interior
+
+
+def test_force_source_emits_half_its_jump():
+    """Reading R15: a planar force layer F (one cell thick, density F N/m^3)
+    makes a pressure jump F dz across it, so it radiates plane waves of
+    pressure +F dz/2 forward and -F dz/2 backward, and velocity F dz/(2 rho0 c0)
+    on both sides (linear, 30 points per wavelength)."""
+    nz, z_src, steps = 160, 70, 700
+    g = oracle.Grid(4, 4, nz, DZ, DZ, DZ, DT, C0, pml_size=(0, 0, 10), pml_alpha=(0, 0, 2.0))
+    sim = oracle.Simulation(g)
+    sim.set_medium(C0, RHO0, 0.0, 0.0)
+    t = np.arange(steps) * DT
+    ramp = np.clip(t * F0 / 3, 0, 1)
+    ramp = 0.5 - 0.5 * np.cos(np.pi * ramp)
+    F = 1e9
+    yy, xx = np.meshgrid(np.arange(4), np.arange(4), indexing="ij")
+    sim.add_source((xx + 4 * (yy + 4 * z_src)).ravel(), F * ramp * np.sin(2 * np.pi * F0 * t), oracle.FORCE_Z)
+    # the force acts at the staggered point z_src + 1/2: pressure probes 45.5 cells
+    # from it on either side, velocity probes (staggered too) 45 cells
+    p_probes, u_probes = [z_src - 45, z_src + 46], [z_src - 45, z_src + 45]
+    rec_p, rec_u = [], []
+    for n in range(steps):
+        sim.step(1)
+        if n >= steps - 200:
+            rec_p.append([sim.p[z, 1, 1] for z in p_probes])
+            rec_u.append([sim.u[2][z, 1, 1] for z in u_probes])
+    rec_p, rec_u = np.array(rec_p), np.array(rec_u)
+    want_p = F * DZ / 2
+    for j in range(2):
+        assert abs(_harmonics(rec_p[:, j], 1)[0] / want_p - 1.0) <= 0.01
+        assert abs(_harmonics(rec_u[:, j], 1)[0] / (want_p / (RHO0 * C0)) - 1.0) <= 0.01
+    # opposite pressure signs on the two sides, the same velocity on both
+    assert np.corrcoef(rec_p[:, 0], rec_p[:, 1])[0, 1] < -0.99
+    assert np.corrcoef(rec_u[:, 0], rec_u[:, 1])[0, 1] > 0.99
