@@ -1,12 +1,22 @@
-// Instantiations of the strided-axis passes: float32 register passes.
-#include "yz_kernel.cuh"
+// Instantiations of the strided-axis passes: float32 register passes.  The z
+// passes of 256- to 1024-point lines use the two-columns-per-thread kernel
+// (z_pair.cuh); shorter lines, and the absorption pass of 1024-point lines,
+// the one-column form of yz_kernel.
+#include "z_pair.cuh"
 
 namespace kwgb {
+
+template <int L, int OP>
+static cudaError_t launch_f32(const YZK& a, int items, cudaStream_t s) {
+    // (1024-point absorption pass: the one-column form measured faster)
+    if constexpr (OP >= OP_Z_GRAD_FWD && L >= 8 && !(L == 10 && OP == OP_Z_ABS)) return launch_pair<L, OP>(a, items, s);
+    else return launch_t<L, OP, 0>(a, items, s);
+}
 
 template <int OP>
 static cudaError_t by_size(const YZK& a, int logn, int items, cudaStream_t s) {
     switch (logn) {
-#define CASE(L) case L: return launch_t<L, OP, 0>(a, items, s);
+#define CASE(L) case L: return launch_f32<L, OP>(a, items, s);
         KWGB_LOG_CASES(CASE)
 #undef CASE
     }

@@ -72,6 +72,14 @@ def test_1024_point_z_lines_in_a_step(kw):
     _compare(kw, cfg, 25)
 
 
+@pytest.mark.parametrize("nz", [256, 512])
+def test_256_and_512_point_z_lines_in_a_step(kw, nz):
+    """The two-columns-per-thread z passes, with a ragged last column pair (nx = 32: 17 columns)."""
+    cfg = _small_cfg((nz, 8, 32), (2, 1, 20), 25)
+    cfg["p0"] = inputs.gaussian_ball(cfg["shape"], 2.0, 1e5, (nz // 2, 4, 16))
+    _compare(kw, cfg, 25)
+
+
 def test_1024_point_y_lines_in_a_step(kw):
     cfg = _small_cfg((8, 1024, 16), (2, 20, 1), 25)
     cfg["p0"] = inputs.gaussian_ball(cfg["shape"], 2.0, 1e5, (4, 512, 8))
