@@ -67,6 +67,23 @@ struct XShape {
     }
 };
 
+// exp(DIR 2 pi i k / (2M)) for k = j + TL*m.  Rows of 1024 reals: one table
+// load per thread (w0 = the value at k = j) times the compile-time root
+// exp(DIR i pi m / E) (TL / M = 1 / E), instead of E loads (measured faster
+// there); shorter rows: the table entry of k, loaded where it is used
+// (measured faster at 512 reals).
+template <int DIR, int M, int E>
+__device__ __forceinline__ float2 row_tw(const float2* __restrict__ tw, float2 w0, int k, int m) {
+    static_assert(E <= 8 && 8 % E == 0, "roots of 16");
+    if constexpr (M >= 512) return rot16<DIR>(w0, m * (8 / E));
+    else return row_twiddle<DIR, M>(tw, k);
+}
+template <int DIR, int M>
+__device__ __forceinline__ float2 row_tw0(const float2* __restrict__ tw, int j) {
+    if constexpr (M >= 512) return row_twiddle<DIR, M>(tw, j);
+    else return make_float2(0.f, 0.f);
+}
+
 // Unnormalised C2R of one row: spec[0..M] (Hermitian half spectrum) ->
 // z[m] = (x[2n], x[2n+1]) with n = j + TL*m and
 // x[i] = sum_{k<nx} X[k] exp(+2 pi i k i / nx).
@@ -87,12 +104,13 @@ __device__ __forceinline__ void row_c2r(const float2* __restrict__ spec, typenam
     for (int m = 0; m < E; ++m) S.at(j + TL * m) = t[m];
     if (j == 0) S.at(M) = nyq;
     S.sync();
+    const float2 w0 = row_tw0<+1, M>(tw, j);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = j + TL * m;
         const float2 xk = S.at(k), xm = cconj(S.at(M - k));
         const float2 a = cadd(xk, xm);
-        const float2 b = cmul(csub(xk, xm), row_twiddle<+1, M>(tw, k));   // exp(+2 pi i k / nx)
+        const float2 b = cmul(csub(xk, xm), row_tw<+1, M, E>(tw, w0, k, m));   // exp(+2 pi i k / nx)
         z[m] = make_float2(a.x - b.y, a.y + b.x);                                // a + i b
     }
     line_fft<LOGM, E, +1>(z, j, S, tw);
@@ -147,12 +165,13 @@ __device__ __forceinline__ void row_c2r_staged(const float2* srow, typename XSha
                                                float2 (&z)[XShape<LOGM>::E]) {
     using Sh = XShape<LOGM>;
     constexpr int M = Sh::M, E = Sh::E, TL = Sh::TL;
+    const float2 w0 = row_tw0<+1, M>(tw, j);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = j + TL * m;
         const float2 xk = srow[k], xm = cconj(srow[M - k]);
         const float2 a = cadd(xk, xm);
-        const float2 b = cmul(csub(xk, xm), row_twiddle<+1, M>(tw, k));   // exp(+2 pi i k / nx)
+        const float2 b = cmul(csub(xk, xm), row_tw<+1, M, E>(tw, w0, k, m));   // exp(+2 pi i k / nx)
         z[m] = make_float2(a.x - b.y, a.y + b.x);                                // a + i b
     }
     S.sync();                                        // previous users of the work row are done
@@ -172,6 +191,7 @@ __device__ __forceinline__ void row_r2c(float2 (&z)[XShape<LOGM>::E], typename X
     for (int m = 0; m < E; ++m) S.at(j + TL * m) = z[m];
     S.sync();
     if (valid) {
+        const float2 w0 = row_tw0<-1, M>(tw, j);
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int k = j + TL * m;
@@ -179,7 +199,7 @@ __device__ __forceinline__ void row_r2c(float2 (&z)[XShape<LOGM>::E], typename X
             const float2 s = cadd(zk, zm), d = csub(zk, zm);
             const float2 xe = make_float2(0.5f * s.x, 0.5f * s.y);
             const float2 xo = make_float2(0.5f * d.y, -0.5f * d.x);              // d / (2i)
-            const float2 x = cadd(xe, cmul(xo, row_twiddle<-1, M>(tw, k)));
+            const float2 x = cadd(xe, cmul(xo, row_tw<-1, M, E>(tw, w0, k, m)));   // exp(-2 pi i k / nx)
             __stcs(spec + k, x);
             if (k == 0) __stcs(spec + M, csub(xe, xo));
         }
