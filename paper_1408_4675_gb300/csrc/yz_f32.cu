@@ -1,15 +1,15 @@
-// Instantiations of the strided-axis passes: float32 register passes.  The z
-// passes of 256- to 1024-point lines use the two-columns-per-thread kernel
-// (z_pair.cuh); shorter lines, and the absorption pass of 1024-point lines,
-// the one-column form of yz_kernel.
+// Instantiations of the strided-axis passes: float32 register passes.  The y
+// and z passes of 256- to 1024-point lines use the two-columns-per-thread
+// kernel (z_pair.cuh); shorter lines, and the y and absorption passes of
+// 1024-point lines, the one-column form of yz_kernel.
 #include "z_pair.cuh"
 
 namespace kwgb {
 
 template <int L, int OP>
 static cudaError_t launch_f32(const YZK& a, int items, cudaStream_t s) {
-    // (1024-point absorption pass: the one-column form measured faster)
-    if constexpr (OP >= OP_Z_GRAD_FWD && L >= 8 && !(L == 10 && OP == OP_Z_ABS)) return launch_pair<L, OP>(a, items, s);
+    // (1024-point y passes and absorption pass: the one-column form measured faster)
+    if constexpr (L >= 8 && !(L == 10 && (OP == OP_Z_ABS || OP < 2))) return launch_pair<L, OP>(a, items, s);
     else return launch_t<L, OP, 0>(a, items, s);
 }
 

@@ -1,11 +1,12 @@
 #pragma once
-// Float32 z pass with two adjacent x-columns per thread (256- to 1024-point
-// z lines).  Same tiles, TMA ring, operators and outputs as the z branch of
+// Float32 y and z passes with two adjacent x-columns per thread (256- to
+// 1024-point lines).  Same tiles, TMA ring, operators and outputs as
 // yz_kernel; the difference is the thread mapping: thread (cp, j) holds
 // elements j + TL*m of columns 2cp and 2cp+1, so
 //   * each twiddle loaded from the table serves two columns,
-//   * every shared-memory access moves both columns' values as one float4
-//     (half the load/store instructions of one column per thread),
+//   * every shared-memory access and every store moves both columns' values
+//     as one float4 (half the load/store instructions of one column per
+//     thread),
 //   * the two columns' transforms are independent instruction streams
 //     that the scheduler interleaves,
 // at half the threads per tile (CTAs of CX/2 * TL threads).
@@ -111,16 +112,16 @@ __device__ __forceinline__ void line_fft_pair(float2 (&va)[E], float2 (&vb)[E], 
 }
 
 // Tiles as in yz_kernel (CX columns, the same TMA boxes); 8 values per
-// column per thread for every line length (1024-point lines: 512 threads).
-template <int LOGN>
+// column per thread for every line length.
+template <int LOGN, bool ISY>
 struct PShape {
-    using Sh = TShape<LOGN, false>;
+    using Sh = TShape<LOGN, ISY>;
     static constexpr int E = 8;
     static constexpr int TL = (1 << LOGN) / E;
     static constexpr int CP = Sh::CX / 2;                      // column pairs per tile
     static constexpr int THREADS = CP * TL;
     static constexpr int SMEM = 3 * Sh::STAGE * (int)sizeof(float2) + 64;
-    static constexpr int MINB = LOGN >= 10 ? 1 : 2;
+    static constexpr int MINB = 3 * Sh::STAGE * (int)sizeof(float2) > 100 * 1024 ? 1 : 2;
     static_assert(THREADS <= 1024, "tile too large");
 };
 
@@ -130,13 +131,15 @@ __device__ __forceinline__ void store_pair(float2* p, float2 a, float2 b, bool v
     else if (v0) __stcs(p, a);
 }
 
+// OP_Y_FWD / OP_Y_INV: the y pass (transform only; items carry the component);
+// z operators: as the z branch of yz_kernel.  (The kernel keeps its z name.)
 template <int LOGN, int OP>
-__global__ void __launch_bounds__(PShape<LOGN>::THREADS, PShape<LOGN>::MINB)
+__global__ void __launch_bounds__(PShape<LOGN, (OP < 2)>::THREADS, PShape<LOGN, (OP < 2)>::MINB)
 z_pair_kernel(const __grid_constant__ YZK a) {
-    using Sh = TShape<LOGN, false>;
-    using Ps = PShape<LOGN>;
+    constexpr bool ISY = OP < 2;
+    using Sh = TShape<LOGN, ISY>;
+    using Ps = PShape<LOGN, ISY>;
     constexpr int E = Ps::E, TL = Ps::TL, CX = Sh::CX, STAGE = Sh::STAGE, CP = Ps::CP;
-    static_assert(OP >= OP_Z_GRAD_FWD, "z operators only");
     extern __shared__ __align__(128) float2 smem[];
     __shared__ int abort_flag;
     float2* scratch = smem + 2 * STAGE;
@@ -145,9 +148,9 @@ z_pair_kernel(const __grid_constant__ YZK a) {
     const int tid = threadIdx.x;
     const int cp = tid % CP, j = tid / CP;
     const int nchunk = (g.nh + CX - 1) / CX;
-    const int lines = g.ny;
-    const int items = nchunk * lines;
-    constexpr int LC = (OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) ? 1 : ((OP == OP_Z_DIV || OP == OP_Z_DIV_FWD) ? 3 : 0);
+    const int lines = ISY ? g.nz : g.ny;
+    const int items = nchunk * lines * (ISY ? a.ncomp : 1);
+    constexpr int LC = (ISY || OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) ? 1 : ((OP == OP_Z_DIV || OP == OP_Z_DIV_FWD) ? 3 : 0);
     const int L = LC ? LC : a.nloads;
     const int my = items > (int)blockIdx.x ? (items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int Q = my * L;
@@ -164,15 +167,18 @@ z_pair_kernel(const __grid_constant__ YZK a) {
         const int item = (int)blockIdx.x + (q / L) * (int)gridDim.x;
         const int l = q % L;
         const int chunk = item % nchunk;
-        const int line = item / nchunk;
-        const int mi = l == 0 ? a.load_comp[0] : (l == 1 ? a.load_comp[1] : a.load_comp[2]);
+        const int line = (item / nchunk) % lines;
+        const int mi = ISY ? item / (nchunk * lines) : (l == 0 ? a.load_comp[0] : (l == 1 ? a.load_comp[1] : a.load_comp[2]));
         const CUtensorMap* map = mi == 0 ? &a.map[0] : (mi == 1 ? &a.map[1] : &a.map[2]);
         float2* dst = smem + (q & 1) * STAGE;
         uint64_t* b = &bar[q & 1];
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(b, STAGE * (uint32_t)sizeof(float2));
 #pragma unroll
-        for (int k = 0; k < Sh::NBOX; ++k) tma_load_3d(dst + k * Sh::BOX * CX, map, chunk * CX, line, k * Sh::BOX, b);
+        for (int k = 0; k < Sh::NBOX; ++k) {
+            if (ISY) tma_load_3d(dst + k * Sh::BOX * CX, map, chunk * CX, k * Sh::BOX, line, b);
+            else tma_load_3d(dst + k * Sh::BOX * CX, map, chunk * CX, line, k * Sh::BOX, b);
+        }
     };
 
     if (tid == 0 && Q > 0) issue(0);
@@ -188,7 +194,7 @@ z_pair_kernel(const __grid_constant__ YZK a) {
         const int item = (int)blockIdx.x + (q / L) * (int)gridDim.x;
         const int l = q % L;
         const int chunk = item % nchunk;
-        const int y = item / nchunk;
+        const int y = (item / nchunk) % lines;               // the line: y for the z pass, z for the y pass
         const int col = chunk * CX + 2 * cp;
         const bool v0 = ok && col < g.nh, v1 = ok && col + 1 < g.nh;
         PairSmem<CX> S{smem + s * STAGE, scratch, cp};
@@ -199,12 +205,19 @@ z_pair_kernel(const __grid_constant__ YZK a) {
             va[m] = make_float2(t.x, t.y);
             vb[m] = make_float2(t.z, t.w);
         }
+        if constexpr (ISY) {
+            const int comp = item / (nchunk * lines);
+            line_fft_pair<LOGN, E, (OP == OP_Y_FWD ? -1 : +1), CX>(va, vb, j, S, g.t.tw);
+            float2* out = out_ptr(a, comp) + (size_t)y * g.ny * g.nhp + col;
+#pragma unroll
+            for (int m = 0; m < E; ++m) store_pair(out + (size_t)(j + TL * m) * g.nhp, va[m], vb[m], v0, v1);
+        } else {
         const size_t es = (size_t)g.ny * g.nhp;
         const size_t off = (size_t)y * g.nhp + col;
         const float kxa = col < g.nh ? __ldg(g.t.kx + col) : 0.f;
         const float kxb = col + 1 < g.nh ? __ldg(g.t.kx + col + 1) : 0.f;
         const float ky = __ldg(g.t.ky + y);
-        if (l == 0) {                            // operator values of this tile, kept for its loads
+        if (!ISY && l == 0) {                    // operator values of this tile, kept for its loads
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const float kz = __ldg(g.t.kz + j + TL * m);
@@ -297,6 +310,7 @@ z_pair_kernel(const __grid_constant__ YZK a) {
 #pragma unroll
             for (int m = 0; m < E; ++m) store_pair(out + (size_t)(j + TL * m) * es, va[m], vb[m], v0, v1);
         }
+        }
         __syncthreads();                          // stage s is free for the load of q + 2
         if (abort_flag) {
             if (tid == 0 && q + 1 < Q) mbar_wait_bounded(&bar[(q + 1) & 1], ((q + 1) >> 1) & 1, a.flag);
@@ -307,7 +321,7 @@ z_pair_kernel(const __grid_constant__ YZK a) {
 
 template <int LOGN, int OP>
 inline cudaError_t launch_pair(const YZK& a, int items, cudaStream_t s) {
-    using Ps = PShape<LOGN>;
+    using Ps = PShape<LOGN, (OP < 2)>;
     auto k = z_pair_kernel<LOGN, OP>;
     static int per_sm = 0;
     if (per_sm == 0) {

@@ -39,7 +39,7 @@ def _sim_for_ops(kw, shape, flags, y):
 
 @pytest.mark.parametrize("shape", [(8, 8, 8), (16, 8, 32), (32, 64, 16), (64, 64, 64),
                                    (8, 16, 1024), (1024, 8, 16), (16, 1024, 8),
-                                   (512, 8, 32), (256, 16, 64)])
+                                   (512, 8, 32), (256, 16, 64), (16, 512, 32), (8, 256, 64)])
 @pytest.mark.parametrize("op", [0, 1, 2, 3])
 def test_spectral_operator_parity(kw, shape, op):
     import torch
