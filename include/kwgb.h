@@ -317,6 +317,14 @@ const char* kwgb_kernel_name(int32_t kind);
  * or KWGB_ERR_CUDA. */
 int kwgb_status(kwgb_sim* sim);
 
+/* Test hook of the failure path: with on != 0 every later tile load of the
+ * y/z passes waits for 16 bytes more than it receives, so its bounded wait
+ * (2 s) runs out; the kernels then skip their stores and return, and
+ * kwgb_status reports KWGB_ERR_TIMEOUT (the CUDA context stays usable).
+ * on = 0 restores normal loads.  No device fault, trap or hang is involved.
+ * Errors: ARG. */
+int kwgb_debug_wait_fault(kwgb_sim* sim, int on);
+
 /* Device bytes held by the simulation. */
 int64_t kwgb_device_bytes(const kwgb_sim* sim);
 

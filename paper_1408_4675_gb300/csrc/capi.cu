@@ -1369,6 +1369,17 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
     return sync_and_flag(sim);
 }
 
+extern "C" int kwgb_debug_wait_fault(kwgb_sim* sim, int on) {
+    if (!sim) return KWGB_ERR_ARG;
+    sim->g.wait_fault_tx = on ? 16u : 0u;
+    if (sim->gexec) {                          // the captured step holds the old parameters
+        cudaGraphExecDestroy(sim->gexec);
+        sim->gexec = nullptr;
+    }
+    sim->graph_off = false;
+    return KWGB_OK;
+}
+
 extern "C" int64_t kwgb_device_bytes(const kwgb_sim* sim) { return sim ? sim->bytes : 0; }
 
 extern "C" const char* kwgb_last_error(const kwgb_sim* sim) {

@@ -41,6 +41,7 @@ struct GridC {
     float abs_c[2];           // kmax^(y-2), kmax^(y-1)
     int num_sms;              // SMs of the device (persistent grids)
     int mixed;                // strided passes: 0 float32, 1 bfloat16-split, 2 float16-split tensor-core products
+    uint32_t wait_fault_tx;   // test hook (kwgb_debug_wait_fault): extra bytes each tile load expects, 0 normally
     Tables t;
 };
 

@@ -173,7 +173,7 @@ z_pair_kernel(const __grid_constant__ YZK a) {
         float2* dst = smem + (q & 1) * STAGE;
         uint64_t* b = &bar[q & 1];
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(b, STAGE * (uint32_t)sizeof(float2));
+        mbar_arrive_expect_tx(b, STAGE * (uint32_t)sizeof(float2) + g.wait_fault_tx);
 #pragma unroll
         for (int k = 0; k < Sh::NBOX; ++k) {
             if (ISY) tma_load_3d(dst + k * Sh::BOX * CX, map, chunk * CX, k * Sh::BOX, line, b);

@@ -93,6 +93,8 @@ def load():
     L.kwgb_save_state.restype = ctypes.c_int
     L.kwgb_load_state.argtypes = [vp, vp, i64]
     L.kwgb_load_state.restype = ctypes.c_int
+    L.kwgb_debug_wait_fault.argtypes = [vp, ctypes.c_int]
+    L.kwgb_debug_wait_fault.restype = ctypes.c_int
     L.kwgb_destroy.argtypes = [vp]
     L.kwgb_destroy.restype = None
     for name in ("kwgb_create", "kwgb_set_allocator", "kwgb_set_medium", "kwgb_set_initial_pressure",
