@@ -20,6 +20,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/kwgb.h"
 #include "kwgb_internal.h"
 
@@ -117,6 +119,14 @@ struct kwgb_sim {
 };
 
 // ------------------------------------------------------------------ helpers
+// NVTX range over one C-ABI call (visible to Nsight tools; a no-op without one)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 static int fail(kwgb_sim* s, int code, const std::string& msg) {
     if (s) s->err = msg;
     return code;
@@ -311,6 +321,7 @@ static int set_field(kwgb_sim* sim, const float* src, bool scalar, bool dev, flo
 
 extern "C" int kwgb_set_medium(kwgb_sim* sim, const float* c0, const float* rho0,
                                const float* b_on_a, const float* alpha0, uint32_t scalar_mask) {
+    NvtxRange nvtx_("kwgb_set_medium");
     if (!sim) return KWGB_ERR_ARG;
     if (sim->medium_set) return fail(sim, KWGB_ERR_STATE, "medium already set");
     if (!c0 || !rho0) return fail(sim, KWGB_ERR_ARG, "c0 and rho0 are required");
@@ -531,6 +542,7 @@ static int run_step(kwgb_sim* sim, cudaStream_t s) {
 
 // ------------------------------------------------------------------ initial pressure
 extern "C" int kwgb_set_initial_pressure(kwgb_sim* sim, const float* p0) {
+    NvtxRange nvtx_("kwgb_set_initial_pressure");
     if (!sim) return KWGB_ERR_ARG;
     if (!p0) return fail(sim, KWGB_ERR_ARG, "p0 is null");
     if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
@@ -805,6 +817,7 @@ static int freeze(kwgb_sim* sim) {
 
 // ------------------------------------------------------------------ stepping
 extern "C" int kwgb_step(kwgb_sim* sim, int64_t n_steps, void* cuda_stream) {
+    NvtxRange nvtx_("kwgb_step");
     if (!sim) return KWGB_ERR_ARG;
     if (n_steps < 0) return fail(sim, KWGB_ERR_ARG, "n_steps < 0");
     if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
@@ -876,6 +889,7 @@ extern "C" int64_t kwgb_state_bytes(kwgb_sim* sim) {
 }
 
 extern "C" int kwgb_save_state(kwgb_sim* sim, void* buf, int64_t len) {
+    NvtxRange nvtx_("kwgb_save_state");
     if (!sim) return KWGB_ERR_ARG;
     if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
     if (int e = freeze(sim)) return e;
@@ -893,6 +907,7 @@ extern "C" int kwgb_save_state(kwgb_sim* sim, void* buf, int64_t len) {
 }
 
 extern "C" int kwgb_load_state(kwgb_sim* sim, const void* buf, int64_t len) {
+    NvtxRange nvtx_("kwgb_load_state");
     if (!sim) return KWGB_ERR_ARG;
     if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
     if (int e = freeze(sim)) return e;
@@ -984,6 +999,7 @@ extern "C" int kwgb_status(kwgb_sim* sim) {
 
 // ------------------------------------------------------------------ reading
 extern "C" int kwgb_read(kwgb_sim* sim, int32_t sensor_id, uint32_t which, double* host_out, int64_t n) {
+    NvtxRange nvtx_("kwgb_read");
     if (!sim) return KWGB_ERR_ARG;
     if (sensor_id < 0 || sensor_id >= (int32_t)sim->hsens.size()) return fail(sim, KWGB_ERR_ARG, "bad sensor id");
     if (!host_out) return fail(sim, KWGB_ERR_ARG, "null output");
@@ -1093,6 +1109,7 @@ extern "C" int kwgb_read_field(kwgb_sim* sim, int field, float* host_out, int64_
 
 extern "C" int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float* out0,
                                    float* out1, float* out2, void* cuda_stream) {
+    NvtxRange nvtx_("kwgb_apply_operator");
     if (!sim) return KWGB_ERR_ARG;
     if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
     if (!in || !out0) return fail(sim, KWGB_ERR_ARG, "null field");
@@ -1158,6 +1175,7 @@ static int copy_dev(kwgb_sim* sim, void* dst, const void* src, size_t bytes, cud
 extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
                             int64_t n_steps, int64_t checkpoint_every, double* J_out, double* grad_out,
                             int64_t grad_len, void* cuda_stream) {
+    NvtxRange nvtx_("kwgb_adjoint");
     if (!sim) return KWGB_ERR_ARG;
     if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
     if (sim->steps != 0 || sim->frozen || sim->adjoint_done)
