@@ -196,6 +196,19 @@ def scale_to(n_from, n_to):
 
 
 # ---------------------------------------------------------------- arms
+def bench_config(cfg, world):
+    """The `config` object of the JSON line (the same for both arms)."""
+    n_points = int(np.prod(cfg["shape"]))
+    return {"workload": workload_name(cfg), "grid": list(cfg["shape"]),
+            "nonlinear": bool(cfg["flags"] & 1), "absorbing": bool(cfg["flags"] & 2),
+            "heterogeneous": not np.isscalar(cfg["c0"]),
+            "l2": ("every field (%d MB) exceeds the 129 MB L2; no flush needed" % (4 * n_points // 10 ** 6)
+                   if 4 * n_points > 129 * 10 ** 6 else
+                   "fields (%d MB) fit in the 129 MB L2: not flushed, small-grid timings include L2 reuse"
+                   % (4 * n_points // 10 ** 6)),
+            "parallelism": "replicas" if world > 1 else "single_gpu"}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -216,7 +229,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(ms, 3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(cfg), "grid": list(cfg["shape"])},
+        "data": "synthetic", "config": bench_config(cfg, world),
         "cpu_baseline": {"value": round(ms, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(ms, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -287,10 +300,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": workload_name(cfg), "grid": list(cfg["shape"]),
-                   "nonlinear": True, "absorbing": True, "heterogeneous": True,
-                   "l2": "every field (>= 537 MB) exceeds the 129 MB L2; no flush needed",
-                   "parallelism": "replicas" if world > 1 else "single_gpu"},
+        "config": bench_config(cfg, world),
         "grid_point_steps_per_s": round(world * N / (ms * 1e-3), 1),
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
