@@ -32,20 +32,19 @@ enum { OP_Y_FWD = 0, OP_Y_INV = 1, OP_Z_GRAD_FWD = 2, OP_Z_GRAD_BWD = 3, OP_Z_DI
 // Column c of a tile in shared memory.  The TMA lands element e of every
 // column as row e (CX float2, dense): raw(e).  The float32 passes (PP)
 // exchange through two buffers, the arrived tile (B = 0) and a scratch tile
-// (B = 1), one barrier per exchange (fft_core.cuh), and swizzle 64-byte rows
-// (CX = 8) as row e ^ ((e >> 3) & 1), so that the first pass, whose warps
-// write rows 8b + q for consecutive b, spreads them over both bank halves.
+// (B = 1), one barrier per exchange (fft_core.cuh).  Rows stay in order: a
+// swizzle against the bank conflicts of the first exchange cost more
+// registers and address arithmetic than the conflicts cost.
 template <int CX, bool PP>
 struct TileSmem {
     float2* buf;              // the arrived tile
     float2* scr;              // scratch tile (PP)
     int c;
     static constexpr bool PINGPONG = PP;
-    __device__ __forceinline__ static int row(int e) { return e; }
     __device__ __forceinline__ float2& at(int e) { return buf[e * CX + c]; }
     __device__ __forceinline__ float2& raw(int e) { return buf[e * CX + c]; }
     template <int B>
-    __device__ __forceinline__ float2& at_pp(int e) { return (B ? scr : buf)[row(e) * CX + c]; }
+    __device__ __forceinline__ float2& at_pp(int e) { return (B ? scr : buf)[e * CX + c]; }
     __device__ __forceinline__ void sync() { __syncthreads(); }
 };
 
