@@ -117,3 +117,25 @@ def test_series_capacity_validation_without_device():
     assert np.all(np.isneginf(sim.read(other, kwgb.P_MAX)))
     assert L.kwgb_add_sensor(sim.h, None, 0, 64, ctypes.byref(ctypes.c_int32())) == -1   # unknown record bit
     sim.close()
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: without libkwgb.so the binding raises instead of computing."""
+    monkeypatch.setattr(kwgb, "LIB_PATH", str(tmp_path / "libkwgb.so"))
+    monkeypatch.setattr(kwgb, "_lib", None)
+    with pytest.raises(ImportError):
+        kwgb.load()
+    with pytest.raises(ImportError):
+        kwgb.Simulation((8, 8, 8), (1e-4, 1e-4, 1e-4), 1e-8, 1500.0)
+
+
+def test_product_package_does_not_reach_the_oracle():
+    """The oracle is test infrastructure: nothing in the package imports or runs it."""
+    pkg = os.path.join(ROOT, "paper_1408_4675_gb300")
+    pat = re.compile(r"^\s*(import\s+oracle\b|from\s+oracle\b)|[\"']oracle/|import_module\([\"']oracle", re.M)
+    for dirpath, dirnames, filenames in os.walk(pkg):
+        dirnames[:] = [d for d in dirnames if not d.startswith(("_", "."))]
+        for fn in filenames:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, fn)).read()
+                assert not pat.search(src), os.path.join(dirpath, fn)
