@@ -7,6 +7,7 @@ paper_1408_4675_gb300.build`` or through ``__graft_entry__.build()``.
 """
 
 import concurrent.futures as cf
+import fcntl
 import hashlib
 import os
 import shutil
@@ -45,8 +46,19 @@ def _digest():
 
 
 def build(verbose=False, force=False):
-    """Compile (if needed) and return the path of libkwgb.so."""
+    """Compile (if needed) and return the path of libkwgb.so.  Processes that
+    build at the same time (one per rank) serialise on a lock file; the ones
+    that wait find the fresh library and return."""
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, "lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, force)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, force):
     stamp = os.path.join(BUILD, "stamp")
     dig = _digest()
     if not force and os.path.exists(LIB) and os.path.exists(stamp):
