@@ -28,6 +28,7 @@ finite differences of the forward oracle.
 from .kspace import (  # noqa: F401
     Grid, Simulation, wavenumbers, kappa, apply_operator, pml_profile,
     NONLINEAR, ABSORBING, P_MAX, P_RMS, I_AVG, P_MIN, P_SERIES, U_SERIES, ADDITIVE_MASS, FORCE_X, FORCE_Y, FORCE_Z,
+    DIRICHLET_P,
     OP_GRAD_FWD, OP_DIV_BWD, OP_ABS_TAU, OP_ABS_ETA,
 )
 from . import adjoint  # noqa: F401,E402

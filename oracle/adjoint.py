@@ -45,6 +45,8 @@ def backward(sim, rec, dJdp):
     the grid) of the objective to the sample p^n, n = 1..Nt.  Returns, for
     every source of `sim` (in add order), dJ/dsignal per source point: an
     (n_points, n_t) array (sum over the points for a shared signal)."""
+    if sim.forces or sim.dirichlet:
+        raise NotImplementedError("the adjoint covers additive mass sources only")
     g = sim.g
     dt = g.dt
     dx = g.d[0]

@@ -66,6 +66,14 @@ the same readings, written independently):
      Eq. 4b (PML included), F^n = the caller's sample n (t = n dt, the time
      level of the right-hand side of Eq. 4b); 0 after the signal ends.  A
      planar force layer radiates pressure +-F dz/2 on its two sides.
+ R16 Dirichlet pressure sources (Sec. 3.4: a source sets the value of the
+     pressure at its grid points): in step n, after the update of Eq. 4d
+     and the additive sources, rho_xi^{n+1} = s / (3 c0^2) for every xi at
+     the mask points, and after Eq. 6, p^{n+1} = s there; s is the caller's
+     sample n, summed over the Dirichlet sources that share a point.  A
+     point is held only in the steps for which one of its signals has a
+     sample; afterwards it evolves freely.  These points enter the
+     absorption term of Eq. 8 with the reset densities.
 """
 
 import os
@@ -85,6 +93,7 @@ U_SERIES = 32
 
 ADDITIVE_MASS = 0
 FORCE_X, FORCE_Y, FORCE_Z = 1, 2, 3
+DIRICHLET_P = 4
 
 OP_GRAD_FWD = 0   # Eq. 4a operator: i k_xi kappa exp(+i k_xi dxi / 2)
 OP_DIV_BWD = 1    # Eq. 4c operator: i k_xi kappa exp(-i k_xi dxi / 2)
@@ -234,6 +243,7 @@ class Simulation:
         self.n = 0
         self.sources = []
         self.forces = []
+        self.dirichlet = []
         self.sensors = []
         self.medium_set = False
         self._build_operators()
@@ -281,10 +291,11 @@ class Simulation:
                   for i in range(3)]
 
     def add_source(self, idx, signal, mode=ADDITIVE_MASS):
-        """Additive mass source (reading R10) or force source along x, y or z
-        (FORCE_X/Y/Z, reading R15) at linear indices idx; signal has shape
-        (n_t,) (shared) or (len(idx), n_t) (per point)."""
-        if mode not in (ADDITIVE_MASS, FORCE_X, FORCE_Y, FORCE_Z):
+        """Additive mass source (reading R10), force source along x, y or z
+        (FORCE_X/Y/Z, reading R15) or Dirichlet pressure source (DIRICHLET_P,
+        reading R16) at linear indices idx; signal has shape (n_t,) (shared)
+        or (len(idx), n_t) (per point)."""
+        if mode not in (ADDITIVE_MASS, FORCE_X, FORCE_Y, FORCE_Z, DIRICHLET_P):
             raise ValueError("unknown source mode")
         idx = np.asarray(idx, dtype=np.int64)
         sig = np.asarray(signal, dtype=np.float64)
@@ -292,9 +303,22 @@ class Simulation:
             sig = np.broadcast_to(sig, (len(idx), sig.shape[0]))
         if mode == ADDITIVE_MASS:
             self.sources.append((idx, sig))
+        elif mode == DIRICHLET_P:
+            self.dirichlet.append((idx, sig))
         else:
             self.forces.append((idx, sig, mode - 1))
-        return len(self.sources) + len(self.forces) - 1
+        return len(self.sources) + len(self.forces) + len(self.dirichlet) - 1
+
+    def _dirichlet_values(self, n):
+        """(points, summed sample) of the Dirichlet sources held in step n (R16)."""
+        val = np.zeros(self.p.size)
+        held = np.zeros(self.p.size, dtype=bool)
+        for idx, sig in self.dirichlet:
+            if n < sig.shape[1]:
+                np.add.at(val, idx, sig[:, n])
+                held[idx] = True
+        pts = np.nonzero(held)[0]
+        return pts, val[pts]
 
     def add_sensor(self, idx=None, record=P_MAX):
         """Sensor at linear indices idx (None = every grid point)."""
@@ -361,6 +385,11 @@ class Simulation:
                 self.rho[i] = num / den                                              # Eq. 4d
                 if src is not None:
                     self.rho[i] = self.rho[i] + src
+            if self.dirichlet:                                                       # R16
+                pts, sv = self._dirichlet_values(self.n)
+                c0f = self.c0.reshape(-1)
+                for i in range(3):
+                    self.rho[i].reshape(-1)[pts] = sv / (3.0 * c0f[pts] ** 2)
             rho = self.rho[0] + self.rho[1] + self.rho[2]
             if g.absorbing:
                 dsum = self.rho0 * (d[0] + d[1] + d[2])
@@ -370,6 +399,8 @@ class Simulation:
                 Ld = 0.0
             nl = (self.bona / 2.0) * rho * rho / self.rho0 if g.nonlinear else 0.0
             self.p = self.c0 ** 2 * (rho + nl - Ld)                                  # Eq. 6
+            if self.dirichlet:
+                self.p.reshape(-1)[pts] = sv                                         # R16
             self.n += 1
             self._record(self.p)
 

@@ -1,7 +1,8 @@
 """Physics pins of the FP64 oracle: the nonlinear coefficient beta = 1 + B/2A
 that Eq. 2 implies (Fubini's pre-shock harmonics of a plane wave), the
-emitted amplitudes of the additive mass source and of the force source, and a PML sanity check (the
-paper gives no PML profile, so the PML itself stays unpinned)."""
+emitted amplitudes of the additive mass source, the force source and the
+Dirichlet pressure source, and a PML sanity check (the paper gives no PML
+profile, so the PML itself stays unpinned)."""
 
 import math
 
@@ -143,3 +144,36 @@ def test_force_source_emits_half_its_jump():
     # opposite pressure signs on the two sides, the same velocity on both
     assert np.corrcoef(rec_p[:, 0], rec_p[:, 1])[0, 1] < -0.99
     assert np.corrcoef(rec_u[:, 0], rec_u[:, 1])[0, 1] > 0.99
+
+
+def test_dirichlet_source_holds_and_radiates_its_value():
+    """Reading R16: a plane whose pressure is held at s(t) radiates plane waves
+    of amplitude s, with the same sign, to both sides (a pressure boundary
+    condition), and the held points take s exactly in every step; once the
+    signal ends the plane evolves freely."""
+    nz, z_src, steps, nt = 160, 70, 700, 650
+    g = oracle.Grid(4, 4, nz, DZ, DZ, DZ, DT, C0, pml_size=(0, 0, 10), pml_alpha=(0, 0, 2.0))
+    sim = oracle.Simulation(g)
+    sim.set_medium(C0, RHO0, 0.0, 0.0)
+    t = (np.arange(nt) + 1) * DT
+    ramp = np.clip(t * F0 / 3, 0, 1)
+    ramp = 0.5 - 0.5 * np.cos(np.pi * ramp)
+    s = 1e5 * ramp * np.sin(2 * np.pi * F0 * t)
+    yy, xx = np.meshgrid(np.arange(4), np.arange(4), indexing="ij")
+    sim.add_source((xx + 4 * (yy + 4 * z_src)).ravel(), s, oracle.DIRICHLET_P)
+    probes = [z_src - 45, z_src + 45]
+    rec = []
+    for n in range(nt):
+        sim.step(1)
+        assert np.all(sim.p[z_src] == s[n])
+        assert np.allclose(sim.rho[0][z_src] + sim.rho[1][z_src] + sim.rho[2][z_src], s[n] / C0 ** 2,
+                           rtol=1e-12, atol=0.0)
+        if n >= nt - 200:
+            rec.append([sim.p[z, 1, 1] for z in probes])
+    rec = np.array(rec)
+    for j in range(2):
+        assert abs(_harmonics(rec[:, j], 1)[0] / 1e5 - 1.0) <= 0.01
+    assert np.corrcoef(rec[:, 0], rec[:, 1])[0, 1] > 0.99
+    held = sim.p[z_src, 1, 1]
+    sim.step(steps - nt)
+    assert sim.p[z_src, 1, 1] != held and abs(sim.p[z_src, 1, 1]) < 2e5
