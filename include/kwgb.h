@@ -67,6 +67,7 @@ extern "C" {
 #define KWGB_FORCE_X 1        /* force density along x, see kwgb_add_source    */
 #define KWGB_FORCE_Y 2
 #define KWGB_FORCE_Z 3
+#define KWGB_DIRICHLET_P 4    /* pressure held at the signal, see kwgb_add_source */
 
 /* ---- objectives of kwgb_adjoint ----------------------------------------- */
 #define KWGB_OBJ_MEAN_ABS_P 0  /* J = 1/(n_obj Nt) sum_{n=1..Nt} sum_i |p^n(idx_i)| */
@@ -157,6 +158,13 @@ int kwgb_set_initial_pressure(kwgb_sim* sim, const float* p0);
  * velocity update of Eq. 4b, u_xi += dt F / rho0_sg at the staggered point of
  * each index, sample n at t = n dt; a planar force layer radiates pressure
  * +-F dxi/2 on its two sides.
+ * mode KWGB_DIRICHLET_P sets the pressure at the points (Sec. 3.4: a source
+ * updates the value of the pressure at its grid points): in step n, after the
+ * density update of Eq. 4d and the additive sources, every split density at
+ * the point becomes s / (3 c0^2), and after Eq. 6 the pressure p^{n+1}
+ * becomes s (sample n; sources sharing a point add); a point is held only in
+ * steps for which one of its signals has a sample.  A plane held this way
+ * radiates plane waves of amplitude s to both sides.
  * *source_id receives the source number.  Errors: ARG (bad mode, sizes,
  * indices), STATE, OOM, CUDA. */
 int kwgb_add_source(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
@@ -261,7 +269,9 @@ int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const float* in, fl
  *              n_signals rows of n_t values dJ/dsignal[row][n]
  * On return the simulation holds the forward end state (n_steps taken) and
  * its sensors hold the forward run's outputs.  Synchronises.
- * Errors: ARG, STATE (already stepped), OOM, CUDA, NONFINITE. */
+ * Errors: ARG, STATE (already stepped), UNSUPPORTED (a force or Dirichlet
+ * source: only additive mass sources are differentiated), OOM, CUDA,
+ * NONFINITE. */
 int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
                  int64_t n_steps, int64_t checkpoint_every, double* J_out, double* grad_out,
                  int64_t grad_len, void* cuda_stream);

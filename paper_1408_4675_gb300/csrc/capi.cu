@@ -88,6 +88,7 @@ struct kwgb_sim {
     std::vector<HostSensor> hsens;
     SourceC src{};              // additive mass sources
     SourceC fsrc[3] = {};       // force sources along x, y, z
+    SourceC dsrc{};             // Dirichlet pressure sources
     bool any_force = false;
     SensorC sens{};
     int64_t n_slots = 0;
@@ -468,17 +469,17 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
         da.S = sim->P;
         da.R = sim->T1;
         da.rho_tot = reinterpret_cast<float*>(sim->T2);
-        LKM(launch_x_dens(g, sim->md, sim->src, sens, st, da, s), K_X_DENS);
+        LKM(launch_x_dens(g, sim->md, sim->src, sim->dsrc, sens, st, da, s), K_X_DENS);
         // Eq. 8: y fwd, z fwd + k^{y-2} / k^{y-1} + z inv, y inv, then Eq. 6
         float2* ab[3] = {sim->P, sim->T1, nullptr};
         LKM(ypass(sim, -1, ab, ab, 2, s), K_Y_FWD_ABS);
         LKM(zop(sim, Z_ABS, ab, ab, s), K_Z_ABS);
         LKM(ypass(sim, +1, ab, ab, 2, s), K_Y_INV_ABS);
         XEosArgs ea{sim->P, sim->T1, reinterpret_cast<float*>(sim->T2), sim->P};
-        LKM(launch_x_eos(g, sim->md, sens, st, ea, s), K_X_EOS);
+        LKM(launch_x_eos(g, sim->md, sim->dsrc, sens, st, ea, s), K_X_EOS);
     } else {
         da.P = sim->P;
-        LKM(launch_x_dens(g, sim->md, sim->src, sens, st, da, s), K_X_DENS);
+        LKM(launch_x_dens(g, sim->md, sim->src, sim->dsrc, sens, st, da, s), K_X_DENS);
     }
     if (sim->n_u || sim->sens.p_min || sim->sens.ser) {
         const SensorC& sc = sim->sens;
@@ -575,7 +576,8 @@ extern "C" int kwgb_add_source(kwgb_sim* sim, const int64_t* idx, int64_t n_idx,
                                int mode, int32_t* source_id) {
     if (!sim) return KWGB_ERR_ARG;
     if (sim->frozen || sim->steps > 0) return fail(sim, KWGB_ERR_STATE, "sources must be added before stepping");
-    if (mode != KWGB_ADDITIVE_MASS && mode != KWGB_FORCE_X && mode != KWGB_FORCE_Y && mode != KWGB_FORCE_Z)
+    if (mode != KWGB_ADDITIVE_MASS && mode != KWGB_FORCE_X && mode != KWGB_FORCE_Y && mode != KWGB_FORCE_Z &&
+        mode != KWGB_DIRICHLET_P)
         return fail(sim, KWGB_ERR_ARG, "unknown source mode");
     if (n_idx < 0 || n_t < 0) return fail(sim, KWGB_ERR_ARG, "negative size");
     if (n_idx > 0 && (!idx || (n_t > 0 && !signal))) return fail(sim, KWGB_ERR_ARG, "null idx or signal");
@@ -701,6 +703,8 @@ static int freeze(kwgb_sim* sim) {
         if (int e = build_sources(sim, KWGB_FORCE_X + a, (float)sim->d.dt, &sim->fsrc[a])) return e;
         sim->any_force |= sim->fsrc[a].row_ptr != nullptr;
     }
+    // Dirichlet: the summed samples themselves
+    if (int e = build_sources(sim, KWGB_DIRICHLET_P, 1.0f, &sim->dsrc)) return e;
     // ---- sensors
     SensorC& sc = sim->sens;
     sc = SensorC{};

@@ -13,13 +13,16 @@ struct XDensK {
     GridC g;
     Medium md;
     SourceC src;
+    SourceC dsrc;             // Dirichlet pressure sources
     SensorC sens;
     StepC st;
     XDensArgs a;
 };
 
 
-template <int LOGM, bool FUSED_EOS>
+// DIRICHLET: the launch has Dirichlet pressure sources (a separate
+// instantiation, so that the common path carries no code for them).
+template <int LOGM, bool FUSED_EOS, bool DIRICHLET>
 __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(const XDensK K) {
     using Sh = XShape<LOGM>;
     using St = XStage<LOGM>;
@@ -132,6 +135,32 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
                 }
             }
         }
+        // Dirichlet pressure sources: rho_xi = s / (3 c0^2) at the held points
+        bool drow = false;
+        float2 dv[E];
+        if (DIRICHLET) {
+            drow = dirichlet_row<LOGM>(K.dsrc, g, S, j, valid, rr, *K.st.step);
+            if (drow) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int x = 2 * (j + TL * m);
+                    dv[m] = make_float2(S.f(x), S.f(x + 1));
+                    const float2 c = med2(md.c0, md.c0_s, rb + x);
+                    if (valid && dv[m].x == dv[m].x) {
+                        const float rx = __fdividef(dv[m].x, c.x * c.x);
+#pragma unroll
+                        for (int xi = 0; xi < 3; ++xi) pick3f(K.a.rho, xi)[rb + x] = rx * (1.0f / 3.0f);
+                        rt[m].x = rx;
+                    }
+                    if (valid && dv[m].y == dv[m].y) {
+                        const float ry = __fdividef(dv[m].y, c.y * c.y);
+#pragma unroll
+                        for (int xi = 0; xi < 3; ++xi) pick3f(K.a.rho, xi)[rb + x + 1] = ry * (1.0f / 3.0f);
+                        rt[m].y = ry;
+                    }
+                }
+            }
+        }
         if (FUSED_EOS) {
             // Eq. 6 without absorption: p = c0^2 (rho + B/2A rho^2 / rho0)
 #pragma unroll
@@ -147,6 +176,10 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
                     q.y += __fdividef(0.5f * ba.y * rho.y * rho.y, r0.y);
                 }
                 s[m] = make_float2(c.x * c.x * q.x, c.y * c.y * q.y);
+                if (DIRICHLET && drow) {                   // p = s at the held points
+                    if (dv[m].x == dv[m].x) s[m].x = dv[m].x;
+                    if (dv[m].y == dv[m].y) s[m].y = dv[m].y;
+                }
             }
             finish_pressure<LOGM>(s, g, K.sens, K.st, S, j, valid, rr, K.a.P);
         } else {
@@ -165,6 +198,7 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
 struct XEosK {
     GridC g;
     Medium md;
+    SourceC dsrc;             // Dirichlet pressure sources
     SensorC sens;
     StepC st;
     XEosArgs a;
@@ -199,7 +233,7 @@ struct XEosStage {
     static constexpr int TEAM = 2 * A + 3 * R;          // per team
 };
 
-template <int LOGM>
+template <int LOGM, bool DIRICHLET>
 __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_eos_kernel(const XEosK K) {
     using Sh = XShape<LOGM>;
     using St = XStage<LOGM>;
@@ -272,6 +306,17 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_eos_kernel(con
         p[m] = make_float2(fmaf(c2[m].x, q.x, fmaf(ce[m].x, a[m].x, acc[m].x)),
                            fmaf(c2[m].y, q.y, fmaf(ce[m].y, a[m].y, acc[m].y)));
     }
+    if (DIRICHLET) {                                     // p = s at the held points
+        if (dirichlet_row<LOGM>(K.dsrc, g, S, j, valid, rr, *K.st.step)) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int x = 2 * (j + TL * m);
+                const float2 dv = make_float2(S.f(x), S.f(x + 1));
+                if (dv.x == dv.x) p[m].x = dv.x;
+                if (dv.y == dv.y) p[m].y = dv.y;
+            }
+        }
+    }
     finish_pressure<LOGM>(p, g, K.sens, K.st, S, j, valid, rr, K.a.P);
 }
 
@@ -320,28 +365,36 @@ __global__ void __launch_bounds__(XTHREADS) x_c2r_kernel(const XPlainK K) {
     }
 }
 
-cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src,
+cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src, const SourceC& dsrc,
                           const SensorC& sens, const StepC& st, const XDensArgs& a,
                           cudaStream_t s) {
-    XDensK K{g, m, src, sens, st, a};
+    XDensK K{g, m, src, dsrc, sens, st, a};
     const bool fused = !m.absorbing;
+    const bool dir = dsrc.row_ptr != nullptr;
     switch (g.lognx - 1) {
 #define CASE(L)                                                                                   \
     case L:                                                                                       \
-        if (fused) return launch_persistent<L>(x_dens_kernel<L, true>, g, K, s); \
-        return launch_persistent<L>(x_dens_kernel<L, false>, g, K, s);
+        if (fused && dir) return launch_persistent<L>(x_dens_kernel<L, true, true>, g, K, s);   \
+        if (fused) return launch_persistent<L>(x_dens_kernel<L, true, false>, g, K, s);         \
+        if (dir) return launch_persistent<L>(x_dens_kernel<L, false, true>, g, K, s);           \
+        return launch_persistent<L>(x_dens_kernel<L, false, false>, g, K, s);
         KWGB_LOGM_CASES(CASE)
 #undef CASE
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_x_eos(const GridC& g, const Medium& m, const SensorC& sens,
+cudaError_t launch_x_eos(const GridC& g, const Medium& m, const SourceC& dsrc, const SensorC& sens,
                          const StepC& st, const XEosArgs& a, cudaStream_t s) {
-    XEosK K{g, m, sens, st, a};
+    XEosK K{g, m, dsrc, sens, st, a};
+    const bool dir = dsrc.row_ptr != nullptr;
     switch (g.lognx - 1) {
-#define CASE(L) \
-    case L: return launch_rows(x_eos_kernel<L>, XShape<L>::RPB, XShape<L>::SMEM + XShape<L>::TPB * XEosStage<L>::TEAM * (int)sizeof(float2), g, K, s);
+#define CASE(L)                                                                                            \
+    case L: {                                                                                              \
+        const int smem = XShape<L>::SMEM + XShape<L>::TPB * XEosStage<L>::TEAM * (int)sizeof(float2);      \
+        if (dir) return launch_rows(x_eos_kernel<L, true>, XShape<L>::RPB, smem, g, K, s);                 \
+        return launch_rows(x_eos_kernel<L, false>, XShape<L>::RPB, smem, g, K, s);                         \
+    }
         KWGB_LOGM_CASES(CASE)
 #undef CASE
     }

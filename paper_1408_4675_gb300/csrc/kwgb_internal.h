@@ -73,7 +73,7 @@ struct SourceC {
     const int32_t* pt_c;      // npts + 1 contribution ranges
     const int64_t* c_off;     // start of the contribution's signal samples
     const int32_t* c_nt;      // number of samples
-    const float* c_scale;     // dt * 2 / (3 c0 dx)
+    const float* c_scale;     // per contribution: dt * 2 / (3 dx) (mass), dt (force), 1 (Dirichlet)
     const float* signal;      // all signal samples
 };
 
@@ -142,7 +142,7 @@ struct XDensArgs {
     float* rho_tot;           // rho as real rows of pitch 2*nhp (absorbing only)
     float2* P;                // non-absorbing: x-R2C of p (EOS fused here)
 };
-cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src,
+cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src, const SourceC& dsrc,
                           const SensorC& sens, const StepC& st, const XDensArgs& a,
                           cudaStream_t s);
 
@@ -152,7 +152,7 @@ struct XEosArgs {
     const float* rho_tot;     // pitch 2*nhp
     float2* P;                // x-R2C of p^{n+1}
 };
-cudaError_t launch_x_eos(const GridC& g, const Medium& m, const SensorC& sens,
+cudaError_t launch_x_eos(const GridC& g, const Medium& m, const SourceC& dsrc, const SensorC& sens,
                          const StepC& st, const XEosArgs& a, cudaStream_t s);
 
 // plain x transforms: real rows (pitch in floats) <-> half spectra (pitch nhp)

@@ -277,6 +277,37 @@ __device__ __forceinline__ void finish_pressure(float2 (&p)[XShape<LOGM>::E], co
     row_r2c<LOGM>(p, S, j, valid, g.t.tw, P + (size_t)row * g.nhp);
 }
 
+// Dirichlet pressure sources of one row in step n: afterwards S.f(x) holds the
+// summed sample of every point x of the row that is held in this step, and
+// NaN at every other x.  All threads of the row's team call it (it contains
+// the team barriers); the result says whether the row has source points
+// (the same for the threads of one row).
+template <int LOGM>
+__device__ __forceinline__ bool dirichlet_row(const SourceC& ds, const GridC& g, typename XShape<LOGM>::Smem& S,
+                                              int j, bool valid, int row, int64_t n) {
+    constexpr int TL = XShape<LOGM>::TL;
+    const int p0 = valid ? __ldg(ds.row_ptr + row) : 0, p1 = valid ? __ldg(ds.row_ptr + row + 1) : 0;
+    S.sync();
+    if (p1 > p0) {
+        for (int x = j; x < g.nx; x += TL) S.f(x) = __int_as_float(0x7fc00000);    // quiet NaN: not held
+    }
+    S.sync();
+    for (int p = p0 + j; p < p1; p += TL) {
+        const int c0 = __ldg(ds.pt_c + p), c1 = __ldg(ds.pt_c + p + 1);
+        float acc = 0.f;
+        bool held = false;
+        for (int c = c0; c < c1; ++c) {
+            if (n < __ldg(ds.c_nt + c)) {
+                acc += __ldg(ds.signal + __ldg(ds.c_off + c) + n) * __ldg(ds.c_scale + c);
+                held = true;
+            }
+        }
+        if (held) S.f(__ldg(ds.pt_x + p)) = acc;
+    }
+    S.sync();
+    return p1 > p0;
+}
+
 // p[i] for a run-time i without copying the parameter array to local memory
 __device__ __forceinline__ const float2* pick3(const float2* const (&p)[3], int i) {
     return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);

@@ -23,6 +23,7 @@ NONLINEAR, ABSORBING = 1, 2
 P_MAX, P_RMS, I_AVG, P_MIN, P_SERIES, U_SERIES = 1, 2, 4, 8, 16, 32
 ADDITIVE_MASS = 0
 FORCE_X, FORCE_Y, FORCE_Z = 1, 2, 3
+DIRICHLET_P = 4
 SCALAR_C0, SCALAR_RHO0, SCALAR_BONA, SCALAR_ALPHA0 = 1, 2, 4, 8
 INPUT_DEVICE = 0x80000000
 FIELD_P, FIELD_UX, FIELD_UY, FIELD_UZ, FIELD_RHOX, FIELD_RHOY, FIELD_RHOZ = range(7)

@@ -255,6 +255,53 @@ def test_force_sources_match_oracle(kw):
     gsim.close()
 
 
+@pytest.mark.parametrize("cfg_id", [2, 5])
+def test_dirichlet_sources_match_oracle(kw, cfg_id):
+    """Dirichlet pressure sources (reading R16): a held plane with a shared
+    signal and held points with their own signals, two of which end before the
+    run does (those points then evolve freely), one overlapping an additive
+    source; in the heterogeneous nonlinear absorbing medium (x_dens then x_eos)
+    and the lossless nonlinear one (the equation of state fused into x_dens).
+    The held points take the float32 signal exactly (seen through p_max: the
+    stored field is the x-transformed p, whose inverse carries FFT rounding)."""
+    steps = 50
+    cfg = inputs.make_config(cfg_id, n=32, n_steps=steps)
+    n = 32
+    yy, xx = np.meshgrid(np.arange(12, 20), np.arange(12, 20), indexing="ij")
+    plane = (xx + n * (yy + n * 11)).ravel()
+    pts = np.array([5 + n * (7 + n * 16), 20 + n * (9 + n * 18), 21 + n * (9 + n * 18)])
+    t = (np.arange(steps) + 1) * cfg["dt"]
+    s1 = 2e5 * np.sin(2 * np.pi * 1e6 * t)
+    s2 = np.stack([1e5 * np.sin(2 * np.pi * 1e6 * t + k) for k in range(3)])
+    s2[1:, 30:] = 0.0
+    sig2 = [s2[0], s2[1, :30], s2[2, :30]]
+    cfg["sources"] = cfg["sources"] + [(plane, s1, kw.DIRICHLET_P), (pts[:1], sig2[0], kw.DIRICHLET_P),
+                                       (pts[1:], np.stack(sig2[1:]), kw.DIRICHLET_P),
+                                       (pts[:1], 3e5 * np.sin(2 * np.pi * 1e6 * t), kw.ADDITIVE_MASS)]
+    cfg["sensors"] = [(np.sort(np.concatenate([plane[::7], pts, pts + 1])), 7), (None, 3)]
+    gsim, gids, osim, oids = _run_both(kw, cfg, steps)
+    _check_outputs(gsim, gids, osim, oids, cfg, 1e-3, 5e-3)
+    _check_fields(gsim, osim, 1e-3, 5e-3)
+    # the sensors see the real-space p of each step: held points exactly the float32 samples
+    sidx = cfg["sensors"][0][0]
+    pmax = gsim.read(gids[0], kw_P_MAX)
+    at = lambda pt: int(np.searchsorted(sidx, pt))
+    for pt in plane[::7]:
+        assert pmax[at(pt)] == np.float32(s1).max()
+    assert pmax[at(pts[0])] == np.float32(s2[0]).max()
+    assert pmax[at(pts[1])] >= np.float32(s2[1, :30]).max()     # held 30 steps, then free
+    gsim.close()
+
+
+def test_adjoint_refuses_dirichlet_sources(kw):
+    cfg = inputs.make_config(1, n=32, n_steps=4)
+    cfg["sources"] = [(np.array([5, 6]), np.ones(4), kw.DIRICHLET_P)]
+    gsim, _ = kw.from_config(cfg)
+    with pytest.raises(kw.KwgbError):
+        gsim.adjoint(np.array([1, 2, 3]), 4, 2)
+    gsim.close()
+
+
 def test_graph_replay_equals_direct_launches(kw):
     """kwgb_step replays a captured CUDA graph after the first step;
     kwgb_step_profiled launches the same kernels directly: the two paths give
