@@ -52,7 +52,11 @@ def test_bench_workload_512_two_steps(kw):
         gsim.close()
 
 
-def test_fused_x_kernels_nx1024(kw):
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_fused_x_kernels_nx1024(kw, dirichlet):
+    """Rows of 1024 reals (two-warp row teams): every fused x kernel, with the
+    additive source, and in the second run Dirichlet points on the same rows
+    (their instantiations of x_dens and x_eos)."""
     cfg = inputs.make_config(2, n=16, n_steps=30)
     shape = (8, 8, 1024)
     cfg["shape"] = shape
@@ -65,6 +69,9 @@ def test_fused_x_kernels_nx1024(kw):
     cfg["pml_size"] = (20, 2, 2)
     cfg["p0"] = inputs.gaussian_ball(shape, 3.0, 5e5, (4, 4, 512))
     cfg["sources"] = [(np.arange(100, 900, 37) + 1024 * (8 * 4 + 3), inputs.cw(1e6, 3e5, cfg["dt"], 30))]
+    if dirichlet:
+        held = np.arange(120, 920, 41) + 1024 * (8 * 5 + 2)
+        cfg["sources"].append((held, inputs.cw(1e6, 2e5, cfg["dt"], 25), kw.DIRICHLET_P))
     cfg["sensors"] = [(None, 3)]
     gsim, gids = kw.from_config(cfg)
     osim, oids = oracle_from_config(cfg)
