@@ -44,7 +44,7 @@ UNIT = "ms/step"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=3, choices=[3, 4])
@@ -135,19 +135,26 @@ def kernel_bytes(cfg):
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (every 50 ms) of the SM clock, power and throttle
+    reasons; the statistics use the samples taken inside [t0, t1] (host clock,
+    set by region()), or all samples if none falls inside."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.idx = gpu_index
+        self.t0 = self.t1 = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+
+    def region(self, t0, t1):
+        self.t0, self.t1 = t0, t1
 
     def stop(self):
         if self.p is None:
@@ -158,31 +165,41 @@ class ClockSampler:
         except Exception:
             self.p.kill()
         self.f.flush()
+        import datetime
         rows = []
         with open(self.f.name) as fh:
             for line in fh:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) >= 10:
+                    try:
+                        ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        ts = None
+                    rows.append([ts] + parts[1:])
         os.unlink(self.f.name)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        inside = [r for r in rows if self.t0 is not None and r[0] is not None and self.t0 <= r[0] <= self.t1]
+        n_all = len(rows)
+        if inside:
+            rows = inside
 
         def num(v):
             try:
                 return float(v)
             except ValueError:
                 return None
-        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
-        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
-        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        # row: timestamp, index, clocks.sm, clocks.max.sm, power.draw, active mask, four reasons
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
+        pw = [num(r[4]) for r in rows if num(r[4]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
         load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
         return {"sm_mhz": statistics.median(load) if load else None,
                 "sm_max_mhz": max(mx) if mx else None,
                 "power_w_max": max(pw) if pw else None,
-                "samples": len(rows), "reasons": reasons}
+                "samples": n_all, "samples_in_timed_region": len(inside), "reasons": reasons}
 
 
 def measured_peaks():
@@ -293,10 +310,12 @@ def run_ours(args):
     l0 = sim.launch_count
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    t_region = time.time()
     ev0.record(stream)
     sim.step(args.steps, stream)
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.region(t_region, time.time())
     reps.barrier()
     launches = sim.launch_count - l0
     ms = ev0.elapsed_time(ev1) / args.steps

@@ -54,3 +54,32 @@ def test_oracle_sample_scaling_is_n_log_n():
 def test_l2_note_follows_the_field_size():
     assert "no flush needed" in bench.bench_config({**_cfg(512, 3), "shape": (512, 512, 512)}, 1)["l2"]
     assert "fit in the 129 MB L2" in bench.bench_config({**_cfg(128, 3), "shape": (128, 128, 128)}, 1)["l2"]
+
+
+def test_clock_record_uses_the_timed_region(tmp_path):
+    """The clocks object summarises the nvidia-smi samples taken while the
+    timed steps ran (median SM clock under load, throttle reasons seen)."""
+    import datetime
+    import time
+    c = bench.ClockSampler.__new__(bench.ClockSampler)
+    c.f = open(tmp_path / "clocks.csv", "w+")
+    now = time.time()
+    for k in range(10):
+        ts = datetime.datetime.fromtimestamp(now + 0.05 * k).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        busy = 3 <= k <= 6
+        c.f.write("%s, 0, %d, 2070, %.1f, 0x0, Not Active, Not Active, Not Active, %s\n"
+                  % (ts, 2070 if busy else 1500, 800.0 if busy else 200.0, "Active" if k == 5 else "Not Active"))
+    c.f.flush()
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            pass
+    c.p = _Proc()
+    c.region(now + 0.14, now + 0.31)
+    out = c.stop()
+    assert out["samples"] == 10 and out["samples_in_timed_region"] == 4
+    assert out["sm_mhz"] == 2070.0 and out["power_w_max"] == 800.0
+    assert out["reasons"] == ["sw_power_cap"]
