@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--profile-case", type=int, nargs=3, metavar=("NZ", "NY", "NX"), default=None,
                     help="small case for ncu captures: a heterogeneous nonlinear absorbing medium on an "
                          "NZ x NY x NX grid stepped --steps times, no timing")
+    ap.add_argument("--profile-flags", type=int, default=0,
+                    help="extra grid flags of the profiling case (4: bfloat16-split, 8: float16-split form)")
     return ap.parse_args()
 
 
@@ -669,7 +671,7 @@ def run_profile_case(args):
     alpha0 = inputs.db_to_neper(inputs.smooth_random_field(shape, 0.3, 1.0, 14, 3.0), 1.1)
     c_ref = float(c0.max())
     sim = kwgb.Simulation(shape, (d, d, d), 0.3 * d / c_ref, c_ref, (10, 10, 10), (2.0, 2.0, 2.0),
-                          flags=3, alpha_power=1.1)
+                          flags=3 | args.profile_flags, alpha_power=1.1)
     sim.set_medium(c0, rho0, bona, alpha0)
     sim.set_initial_pressure(inputs.gaussian_ball(shape, 3.0, 1e5))
     sim.add_sensor(inputs.box_mask(shape, tuple(n // 2 for n in shape), 4), 3)

@@ -100,24 +100,72 @@ __device__ __forceinline__ void dft8_matrix(int lane, uint32_t (&ah)[4], uint32_
     split2<PREC>(c[0], c[1], ah[3], al[3]);
 }
 
+// Layout of a tile between two tensor-core stages (the first stage reads and
+// the last writes the plain layout [e][c] that the TMA and the float32 code
+// use).  A stage's lanes (g = lane / 4, t = lane % 4) read rows b + (2t + d) N/8
+// of four columns and write rows base + g NS of four columns; in the plain
+// layout the four rows of a half-warp fall on the same banks (64-bit accesses
+// are served per half-warp: four-way conflicts).  Here element (e, c) sits at
+// row e ^ P(e), column c ^ H(e), with P and H bits formed as parities of row
+// bits:
+//   A = bits {0, 3, 6, 9}     separates the rows g NS of a write (with C),
+//   C = bits {1, 4, 7, 10}    (plus bit Q+1 when it holds neither Q nor Q+1),
+//   B = bit Q or Q+1          separates the rows b + (2t + d) N/8 of a read
+//                             (with C), Q = log2 N - 2;
+// 16 columns: H = A | B << 2 | C << 3, P = 0; 8 columns (a row is 16 banks):
+// H = A | B << 2 and P = C flips the row's bank half.  Every access of every
+// stage of the tiles used here is then one wavefront per half-warp (checked by
+// enumerating the accesses).  A, B, C are parities, hence XOR-linear: for rows
+// whose parts occupy disjoint bits, H(x + y) = H(x) ^ H(y), so the per-lane
+// parts are computed once.
+template <int LOGN, int CX>
+struct TcSwz {
+    static_assert(CX == 8 || CX == 16, "tile width");
+    static constexpr int Q = LOGN - 2;
+    static constexpr uint32_t A = 0x249u;
+    static constexpr uint32_t C0 = 0x492u;
+    static constexpr uint32_t C = ((C0 >> Q) & 3u) ? C0 : (C0 | (1u << (Q + 1)));
+    static constexpr uint32_t B = ((C >> (Q + 1)) & 1u) ? (1u << Q) : (1u << (Q + 1));
+    __device__ __forceinline__ static int par(uint32_t m, int r) { return __popc((uint32_t)r & m) & 1; }
+    __device__ __forceinline__ static int hcol(int r) {
+        return par(A, r) | (par(B, r) << 2) | (CX == 16 ? (par(C, r) << 3) : 0);
+    }
+    __device__ __forceinline__ static int hrow(int r) { return CX == 8 ? par(C, r) : 0; }
+    // index of (row, col) given the row's H and P
+    __device__ __forceinline__ static int at(int row, int col, int h, int p) { return (row ^ p) * CX + (col ^ h); }
+};
+
 // One radix-8 Stockham stage (stride NS) of a tile, on the tensor cores.
 // Butterfly beta = 32 w + 8 G + n (column c = beta % CX, butterfly b = beta / CX).
-template <int N, int CX, int NS, int DIR, int THREADS, int PREC>
+// IN_SW / OUT_SW: the stage reads / writes the TcSwz layout (else plain).
+template <int N, int CX, int NS, int DIR, int THREADS, int PREC, bool IN_SW, bool OUT_SW>
 __device__ __forceinline__ void tc_stage8(float2* buf, const uint32_t (&ah)[4], const uint32_t (&al)[4],
                                           const float2* __restrict__ tw, const float* colscale) {
     constexpr int NBF = CX * N / 8;                           // butterflies in the tile
     constexpr int WARPS = THREADS / 32;
     constexpr int GROUPS = NBF / (8 * WARPS);                 // 8-butterfly groups per warp
     static_assert(NBF % (8 * WARPS) == 0, "tile / warp split");
+    using L = TcSwz<ilog2c(N), CX>;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
+    // per-lane parts of the swizzle: read rows b + (2t + d) N/8, write rows base + g NS
+    const int rr0 = (2 * t) * (N / 8), rr1 = (2 * t + 1) * (N / 8);
+    const int hr0 = L::hcol(rr0), pr0 = L::hrow(rr0), hr1 = L::hcol(rr1), pr1 = L::hrow(rr1);
+    const int hw = L::hcol(g * NS), pw = L::hrow(g * NS);
     float d[GROUPS][4];
 #pragma unroll
     for (int G = 0; G < GROUPS; ++G) {
         const int beta = (w * GROUPS + G) * 8 + g;            // this lane's B column
         const int c = beta % CX, b = beta / CX;
-        float2 x0 = buf[(b + (2 * t) * (N / 8)) * CX + c];
-        float2 x1 = buf[(b + (2 * t + 1) * (N / 8)) * CX + c];
+        float2 x0, x1;
+        if (IN_SW) {
+            const int hb = L::hcol(b), pb = L::hrow(b);
+            x0 = buf[L::at(b + rr0, c, hb ^ hr0, pb ^ pr0)];
+            x1 = buf[L::at(b + rr1, c, hb ^ hr1, pb ^ pr1)];
+        } else {
+            x0 = buf[(b + rr0) * CX + c];
+            x1 = buf[(b + rr1) * CX + c];
+        }
         if (NS > 1) {
             const int k = b & (NS - 1);
             x0 = cmul(x0, twiddle1024<DIR>(tw, k * (2 * t) * (1024 / (NS * 8))));
@@ -145,16 +193,20 @@ __device__ __forceinline__ void tc_stage8(float2* buf, const uint32_t (&ah)[4], 
             const int c = beta % CX, b = beta / CX;
             const int base = (b / NS) * NS * 8 + (b & (NS - 1));
             const float us = PREC == 2 ? 1.0f / colscale[c] : 1.0f;           // exact: a power of two
-            buf[(base + g * NS) * CX + c] = make_float2(d[G][i] * us, d[G][2 + i] * us);
+            const float2 o = make_float2(d[G][i] * us, d[G][2 + i] * us);
+            if (OUT_SW) buf[L::at(base + g * NS, c, L::hcol(base) ^ hw, L::hrow(base) ^ pw)] = o;
+            else buf[(base + g * NS) * CX + c] = o;
         }
     }
     __syncthreads();
 }
 
-// A float32 radix-RP Stockham stage (RP = 2 or 4) on the tile in shared memory.
-template <int N, int CX, int RP, int NS, int DIR, int THREADS>
+// A float32 radix-RP Stockham stage (RP = 2 or 4) on the tile in shared memory;
+// the last stage of a transform, reading the TcSwz layout when IN_SW.
+template <int N, int CX, int RP, int NS, int DIR, int THREADS, bool IN_SW>
 __device__ __forceinline__ void f32_stage(float2* buf, const float2* __restrict__ tw) {
     constexpr int NBF = CX * N / RP;
+    using L = TcSwz<ilog2c(N), CX>;
     float2 o[(NBF + THREADS - 1) / THREADS][RP];
 #pragma unroll
     for (int q = 0; q < (NBF + THREADS - 1) / THREADS; ++q) {
@@ -163,7 +215,10 @@ __device__ __forceinline__ void f32_stage(float2* buf, const float2* __restrict_
             const int c = beta % CX, b = beta / CX;
             float2 v[RP];
 #pragma unroll
-            for (int r = 0; r < RP; ++r) v[r] = buf[(b + r * (N / RP)) * CX + c];
+            for (int r = 0; r < RP; ++r) {
+                const int row = b + r * (N / RP);
+                v[r] = IN_SW ? buf[L::at(row, c, L::hcol(row), L::hrow(row))] : buf[row * CX + c];
+            }
             if (NS > 1) {
                 const int k = b & (NS - 1);
 #pragma unroll
@@ -196,10 +251,10 @@ struct TcChain {
         constexpr int N = 1 << LOGN;
         constexpr int REM = N / NS;
         if constexpr (REM >= 8) {
-            tc_stage8<N, CX, NS, DIR, THREADS, PREC>(buf, ah, al, tw, colscale);
+            tc_stage8<N, CX, NS, DIR, THREADS, PREC, (NS > 1), (NS * 8 < N)>(buf, ah, al, tw, colscale);
             TcChain<LOGN, CX, DIR, THREADS, PREC, NS * 8>::run(buf, ah, al, tw, colscale);
         } else {
-            f32_stage<N, CX, (REM >= 4 ? 4 : 2), NS, DIR, THREADS>(buf, tw);
+            f32_stage<N, CX, (REM >= 4 ? 4 : 2), NS, DIR, THREADS, (NS > 1)>(buf, tw);
         }
     }
 };
