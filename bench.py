@@ -368,6 +368,8 @@ def run_ours(args):
         out["mixed_f16"] = step_variant(args, kwgb, torch, 3, 8)
         out["mixed_bf16"] = step_variant(args, kwgb, torch, 3, 4)
         out["also_1024"] = step_variant(args, kwgb, torch, 4, 0)
+        out["mixed_f16_1024"] = step_variant(args, kwgb, torch, 4, 8)
+        out["mixed_bf16_1024"] = step_variant(args, kwgb, torch, 4, 4)
         out["linear_lossless_512"] = step_variant(args, kwgb, torch, 3, 0, _linear_lossless,
                                                   "float32, linear lossless (10 FFTs, EOS fused into x_dens)")
         out["homogeneous_512"] = step_variant(args, kwgb, torch, 3, 0, _homogeneous,

@@ -26,6 +26,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "fft_core.cuh"
 
 namespace kwgb {
@@ -133,39 +135,71 @@ struct TcSwz {
     __device__ __forceinline__ static int hrow(int r) { return CX == 8 ? par(C, r) : 0; }
     // index of (row, col) given the row's H and P
     __device__ __forceinline__ static int at(int row, int col, int h, int p) { return (row ^ p) * CX + (col ^ h); }
+    __device__ __forceinline__ static int idx(int row, int col) { return at(row, col, hcol(row), hrow(row)); }
 };
+
+// A tile layout given by its masks: bit k of H is the parity of the row bits in
+// Mk, P the parity of the row bits in MP (element (e, c) at row e ^ P(e),
+// column c ^ H(e), as in TcSwz).  MP must not hold bit 0, so that the row map
+// is a bijection.  All masks zero: the plain layout [e][c].
+template <int CX, uint32_t M0, uint32_t M1, uint32_t M2, uint32_t M3, uint32_t MP>
+struct TcXor {
+    static_assert(CX == 8 || CX == 16, "tile width");
+    static_assert((CX == 16 || M3 == 0) && (CX == 8 || MP == 0) && (MP & 1u) == 0, "layout masks");
+    __device__ __forceinline__ static int par(uint32_t m, int r) { return m ? (__popc((uint32_t)r & m) & 1) : 0; }
+    __device__ __forceinline__ static int hcol(int r) {
+        return par(M0, r) | (par(M1, r) << 1) | (par(M2, r) << 2) | (par(M3, r) << 3);
+    }
+    __device__ __forceinline__ static int hrow(int r) { return par(MP, r); }
+    __device__ __forceinline__ static int at(int row, int col, int h, int p) { return (row ^ p) * CX + (col ^ h); }
+    __device__ __forceinline__ static int idx(int row, int col) { return at(row, col, hcol(row), hrow(row)); }
+};
+template <int CX>
+using TcPlain = TcXor<CX, 0u, 0u, 0u, 0u, 0u>;
+
+// Layouts of the 512- and 1024-point transforms (radix-8 stage of stride 1,
+// then the strides 8 and 64 in one pass, see tc_stage8x8).  With G = log2 N - 6
+// and T = log2 N - 2:
+//   TcMid (written by the first stage, read by the fused pass):
+//     H0 = b0 ^ bG, H1 = b(G+1), H2 = bT, and H3 = b1 ^ b(T+1) (16 columns)
+//     or P = b1 ^ b(T+1) (8 columns).  The first stage's writes vary row bits
+//     0, 1 and column bits 1, 2 within a half-warp, the fused pass's reads row
+//     bits G, G+1, T, T+1 in one column: both meet 16 distinct bank pairs.
+//   TcOut (written by the fused pass): H = (b4, b5, b6) and H3 = b7 or P = b7.
+//     The fused pass's writes vary row bits 4..7 in one column; the readers
+//     after it (the radix-2 float32 stage, the kernel's copy-out) vary the
+//     column and row bit 0 only, which no mask holds.
+// (Every access of the three tile shapes used was checked by enumeration.)
+template <int LOGN, int CX>
+using TcMid = TcXor<CX, 1u | (1u << (LOGN - 6)), 1u << (LOGN - 5), 1u << (LOGN - 2),
+                    CX == 16 ? (2u | (1u << (LOGN - 1))) : 0u, CX == 8 ? (2u | (1u << (LOGN - 1))) : 0u>;
+template <int CX>
+using TcOut = TcXor<CX, 1u << 4, 1u << 5, 1u << 6, CX == 16 ? (1u << 7) : 0u, CX == 8 ? (1u << 7) : 0u>;
 
 // One radix-8 Stockham stage (stride NS) of a tile, on the tensor cores.
 // Butterfly beta = 32 w + 8 G + n (column c = beta % CX, butterfly b = beta / CX).
-// IN_SW / OUT_SW: the stage reads / writes the TcSwz layout (else plain).
-template <int N, int CX, int NS, int DIR, int THREADS, int PREC, bool IN_SW, bool OUT_SW>
+// LI / LO: the layouts the stage reads and writes (TcSwz, TcXor).
+template <int N, int CX, int NS, int DIR, int THREADS, int PREC, class LI, class LO>
 __device__ __forceinline__ void tc_stage8(float2* buf, const uint32_t (&ah)[4], const uint32_t (&al)[4],
                                           const float2* __restrict__ tw, const float* colscale) {
     constexpr int NBF = CX * N / 8;                           // butterflies in the tile
     constexpr int WARPS = THREADS / 32;
     constexpr int GROUPS = NBF / (8 * WARPS);                 // 8-butterfly groups per warp
     static_assert(NBF % (8 * WARPS) == 0, "tile / warp split");
-    using L = TcSwz<ilog2c(N), CX>;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    // per-lane parts of the swizzle: read rows b + (2t + d) N/8, write rows base + g NS
+    // per-lane parts of the layouts: read rows b + (2t + d) N/8, write rows base + g NS
     const int rr0 = (2 * t) * (N / 8), rr1 = (2 * t + 1) * (N / 8);
-    const int hr0 = L::hcol(rr0), pr0 = L::hrow(rr0), hr1 = L::hcol(rr1), pr1 = L::hrow(rr1);
-    const int hw = L::hcol(g * NS), pw = L::hrow(g * NS);
+    const int hr0 = LI::hcol(rr0), pr0 = LI::hrow(rr0), hr1 = LI::hcol(rr1), pr1 = LI::hrow(rr1);
+    const int hw = LO::hcol(g * NS), pw = LO::hrow(g * NS);
     float d[GROUPS][4];
 #pragma unroll
     for (int G = 0; G < GROUPS; ++G) {
         const int beta = (w * GROUPS + G) * 8 + g;            // this lane's B column
         const int c = beta % CX, b = beta / CX;
-        float2 x0, x1;
-        if (IN_SW) {
-            const int hb = L::hcol(b), pb = L::hrow(b);
-            x0 = buf[L::at(b + rr0, c, hb ^ hr0, pb ^ pr0)];
-            x1 = buf[L::at(b + rr1, c, hb ^ hr1, pb ^ pr1)];
-        } else {
-            x0 = buf[(b + rr0) * CX + c];
-            x1 = buf[(b + rr1) * CX + c];
-        }
+        const int hb = LI::hcol(b), pb = LI::hrow(b);
+        float2 x0 = buf[LI::at(b + rr0, c, hb ^ hr0, pb ^ pr0)];
+        float2 x1 = buf[LI::at(b + rr1, c, hb ^ hr1, pb ^ pr1)];
         if (NS > 1) {
             const int k = b & (NS - 1);
             x0 = cmul(x0, twiddle1024<DIR>(tw, k * (2 * t) * (1024 / (NS * 8))));
@@ -194,19 +228,17 @@ __device__ __forceinline__ void tc_stage8(float2* buf, const uint32_t (&ah)[4], 
             const int base = (b / NS) * NS * 8 + (b & (NS - 1));
             const float us = PREC == 2 ? 1.0f / colscale[c] : 1.0f;           // exact: a power of two
             const float2 o = make_float2(d[G][i] * us, d[G][2 + i] * us);
-            if (OUT_SW) buf[L::at(base + g * NS, c, L::hcol(base) ^ hw, L::hrow(base) ^ pw)] = o;
-            else buf[(base + g * NS) * CX + c] = o;
+            buf[LO::at(base + g * NS, c, LO::hcol(base) ^ hw, LO::hrow(base) ^ pw)] = o;
         }
     }
     __syncthreads();
 }
 
 // A float32 radix-RP Stockham stage (RP = 2 or 4) on the tile in shared memory;
-// the last stage of a transform, reading the TcSwz layout when IN_SW.
-template <int N, int CX, int RP, int NS, int DIR, int THREADS, bool IN_SW>
+// the last stage of a transform: reads layout LI, writes the plain layout.
+template <int N, int CX, int RP, int NS, int DIR, int THREADS, class LI>
 __device__ __forceinline__ void f32_stage(float2* buf, const float2* __restrict__ tw) {
     constexpr int NBF = CX * N / RP;
-    using L = TcSwz<ilog2c(N), CX>;
     float2 o[(NBF + THREADS - 1) / THREADS][RP];
 #pragma unroll
     for (int q = 0; q < (NBF + THREADS - 1) / THREADS; ++q) {
@@ -217,7 +249,7 @@ __device__ __forceinline__ void f32_stage(float2* buf, const float2* __restrict_
 #pragma unroll
             for (int r = 0; r < RP; ++r) {
                 const int row = b + r * (N / RP);
-                v[r] = IN_SW ? buf[L::at(row, c, L::hcol(row), L::hrow(row))] : buf[row * CX + c];
+                v[r] = buf[LI::idx(row, c)];
             }
             if (NS > 1) {
                 const int k = b & (NS - 1);
@@ -243,6 +275,85 @@ __device__ __forceinline__ void f32_stage(float2* buf, const float2* __restrict_
     __syncthreads();
 }
 
+// The radix-8 stages of strides 8 and 64 of a 512- or 1024-point transform in
+// one pass through shared memory.  A group is one tile column c and one
+// B0 < N/64 (alpha = B0 % 8, beta = B0 / 8).  Stage a (stride 8) takes the
+// butterflies B0 + r N/64, r = 0..7, as the eight B columns of one product;
+// stage b (stride 64) takes the butterflies 64 beta + 8 q + alpha, q = 0..7,
+// whose input r is output q of stage-a butterfly r.  The m16n8k16 accumulator
+// leaves output g of B columns 2t, 2t + 1 in lane (g, t), and the next B
+// fragment of that lane is inputs 2t, 2t + 1 of B column g: the same values.
+// So the 64-point sub-transforms stay in registers; between the two products
+// only the stage-b twiddles are applied (and the operands split again).
+// Reads layout LI (TcMid), writes LO (TcOut).  Float16-split: the column scale
+// is applied once before stage a and removed after stage b (the values grow at
+// most 64x in between, which float16 holds at the [32, 64) input scale).
+template <int N, int CX, int DIR, int THREADS, int PREC, class LI, class LO>
+__device__ __forceinline__ void tc_stage8x8(float2* buf, const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                            const float2* __restrict__ tw, const float* colscale) {
+    static_assert(N == 512 || N == 1024, "strides 8 and 64 of a 512- or 1024-point line");
+    constexpr int WARPS = THREADS / 32;
+    constexpr int GROUPS = CX * (N / 64) / WARPS;            // groups per warp
+    static_assert((CX * (N / 64)) % WARPS == 0, "tile / warp split");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    // per-lane parts of the layouts (the parts of a row occupy disjoint bits):
+    // reads rows B0 + g N/64 + (2t + d) N/8, writes rows 512 beta + alpha + 8 (2t + i) + 64 g
+    const int rg = g * (N / 64), r0 = (2 * t) * (N / 8), r1 = (2 * t + 1) * (N / 8);
+    const int h0 = LI::hcol(rg) ^ LI::hcol(r0), p0 = LI::hrow(rg) ^ LI::hrow(r0);
+    const int h1 = LI::hcol(rg) ^ LI::hcol(r1), p1 = LI::hrow(rg) ^ LI::hrow(r1);
+    const int wr0 = 16 * t + 64 * g, wr1 = 16 * t + 8 + 64 * g;
+    const int wh0 = LO::hcol(16 * t) ^ LO::hcol(64 * g), wp0 = LO::hrow(16 * t) ^ LO::hrow(64 * g);
+    const int wh1 = LO::hcol(16 * t + 8) ^ LO::hcol(64 * g), wp1 = LO::hrow(16 * t + 8) ^ LO::hrow(64 * g);
+    float d[GROUPS][4];
+#pragma unroll
+    for (int G = 0; G < GROUPS; ++G) {
+        const int grp = w * GROUPS + G;
+        const int c = grp % CX, B0 = grp / CX, alpha = B0 & 7;
+        const int hb = LI::hcol(B0), pb = LI::hrow(B0);
+        float2 x0 = buf[LI::at(B0 + rg + r0, c, hb ^ h0, pb ^ p0)];
+        float2 x1 = buf[LI::at(B0 + rg + r1, c, hb ^ h1, pb ^ p1)];
+        // stage a: input m of a butterfly with b % 8 = alpha times exp(DIR 2 pi i alpha m / 64)
+        x0 = cmul(x0, twiddle1024<DIR>(tw, alpha * (2 * t) * 16));
+        x1 = cmul(x1, twiddle1024<DIR>(tw, alpha * (2 * t + 1) * 16));
+        if (PREC == 2) {
+            const float sc = colscale[c];
+            x0 = cscale(x0, sc);
+            x1 = cscale(x1, sc);
+        }
+        uint32_t bh0, bl0, bh1, bl1;
+        split2<PREC>(x0.x, x1.x, bh0, bl0);
+        split2<PREC>(x0.y, x1.y, bh1, bl1);
+        float e[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_16816<PREC>(e, al, bh0, bh1);
+        mma_16816<PREC>(e, ah, bl0, bl1);
+        mma_16816<PREC>(e, ah, bh0, bh1);
+        // stage b: butterfly 64 beta + 8 g + alpha, input r (= 2t, 2t + 1) times
+        // exp(DIR 2 pi i (8 g + alpha) r / 512)
+        const int kb = 8 * g + alpha;
+        const float2 y0 = cmul(make_float2(e[0], e[2]), twiddle1024<DIR>(tw, kb * (2 * t) * 2));
+        const float2 y1 = cmul(make_float2(e[1], e[3]), twiddle1024<DIR>(tw, kb * (2 * t + 1) * 2));
+        split2<PREC>(y0.x, y1.x, bh0, bl0);
+        split2<PREC>(y0.y, y1.y, bh1, bl1);
+        d[G][0] = d[G][1] = d[G][2] = d[G][3] = 0.f;
+        mma_16816<PREC>(d[G], al, bh0, bh1);
+        mma_16816<PREC>(d[G], ah, bl0, bl1);
+        mma_16816<PREC>(d[G], ah, bh0, bh1);
+    }
+    __syncthreads();                                          // all inputs read
+#pragma unroll
+    for (int G = 0; G < GROUPS; ++G) {
+        const int grp = w * GROUPS + G;
+        const int c = grp % CX, B0 = grp / CX;
+        const int rb = 512 * (B0 >> 3) + (B0 & 7);
+        const int hb = LO::hcol(rb), pb = LO::hrow(rb);
+        const float us = PREC == 2 ? 1.0f / colscale[c] : 1.0f;               // exact: a power of two
+        buf[LO::at(rb + wr0, c, hb ^ wh0, pb ^ wp0)] = make_float2(d[G][0] * us, d[G][2] * us);
+        buf[LO::at(rb + wr1, c, hb ^ wh1, pb ^ wp1)] = make_float2(d[G][1] * us, d[G][3] * us);
+    }
+    __syncthreads();
+}
+
 // Radix-8 tensor-core stages while they fit, then one float32 stage of the rest.
 template <int LOGN, int CX, int DIR, int THREADS, int PREC, int NS>
 struct TcChain {
@@ -251,10 +362,13 @@ struct TcChain {
         constexpr int N = 1 << LOGN;
         constexpr int REM = N / NS;
         if constexpr (REM >= 8) {
-            tc_stage8<N, CX, NS, DIR, THREADS, PREC, (NS > 1), (NS * 8 < N)>(buf, ah, al, tw, colscale);
+            using LI = std::conditional_t<(NS > 1), TcSwz<LOGN, CX>, TcPlain<CX>>;
+            using LO = std::conditional_t<(NS * 8 < N), TcSwz<LOGN, CX>, TcPlain<CX>>;
+            tc_stage8<N, CX, NS, DIR, THREADS, PREC, LI, LO>(buf, ah, al, tw, colscale);
             TcChain<LOGN, CX, DIR, THREADS, PREC, NS * 8>::run(buf, ah, al, tw, colscale);
         } else {
-            f32_stage<N, CX, (REM >= 4 ? 4 : 2), NS, DIR, THREADS, (NS > 1)>(buf, tw);
+            using LI = std::conditional_t<(NS > 1), TcSwz<LOGN, CX>, TcPlain<CX>>;
+            f32_stage<N, CX, (REM >= 4 ? 4 : 2), NS, DIR, THREADS, LI>(buf, tw);
         }
     }
 };
@@ -264,7 +378,8 @@ struct TcChain<LOGN, CX, DIR, THREADS, PREC, (1 << LOGN)> {
                                                const float2*, const float*) {}
 };
 
-// In-place unnormalised DFT of every column of the tile (natural order in and out).
+// In-place unnormalised DFT of every column of the tile (natural order in and
+// out; the input in the plain layout, the result in layout TcResult).
 // Starts and ends with the tile fully written (callers synchronise before).
 // colscale: CX floats of shared memory (used by PREC 2).
 template <int LOGN, int CX, int DIR, int THREADS, int PREC>
@@ -274,14 +389,22 @@ __device__ __forceinline__ void tile_fft_tc(float2* buf, const float2* __restric
     if constexpr (PREC == 2) {
         // per column: largest |Re|, |Im| -> power-of-two scale to [32, 64)
         constexpr int N = 1 << LOGN;
+        static_assert(THREADS % CX == 0 && CX <= 32 && (N * CX) % THREADS == 0, "column of a thread");
         unsigned int* cm = reinterpret_cast<unsigned int*>(colscale);
         if (threadIdx.x < CX) cm[threadIdx.x] = 0u;
         __syncthreads();
+        // every element a thread visits lies in column threadIdx.x % CX: a local
+        // maximum, then a butterfly over the lanes of the same column, then one
+        // shared atomic per column and warp
+        float m = 0.f;
+#pragma unroll 4
         for (int i = threadIdx.x; i < N * CX; i += THREADS) {
             const float2 v = buf[i];
-            const float m = fmaxf(fabsf(v.x), fabsf(v.y));
-            atomicMax(cm + (i % CX), __float_as_uint(m));      // non-negative floats order as integers
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
+#pragma unroll
+        for (int o = CX; o < 32; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) < CX) atomicMax(cm + (threadIdx.x % CX), __float_as_uint(m));   // non-negative floats order as integers
         __syncthreads();
         if (threadIdx.x < CX) {
             const float m = __uint_as_float(cm[threadIdx.x]);
@@ -291,7 +414,20 @@ __device__ __forceinline__ void tile_fft_tc(float2* buf, const float2* __restric
         }
         __syncthreads();
     }
-    TcChain<LOGN, CX, DIR, THREADS, PREC, 1>::run(buf, ah, al, tw, colscale);
+    if constexpr (LOGN == 9 || LOGN == 10) {
+        // stride 1, then strides 8 and 64 in one pass, then (1024) a float32 radix-2 stage
+        constexpr int N = 1 << LOGN;
+        tc_stage8<N, CX, 1, DIR, THREADS, PREC, TcPlain<CX>, TcMid<LOGN, CX>>(buf, ah, al, tw, colscale);
+        tc_stage8x8<N, CX, DIR, THREADS, PREC, TcMid<LOGN, CX>, TcOut<CX>>(buf, ah, al, tw, colscale);
+        if constexpr (LOGN == 10) f32_stage<N, CX, 2, 512, DIR, THREADS, TcOut<CX>>(buf, tw);
+    } else {
+        TcChain<LOGN, CX, DIR, THREADS, PREC, 1>::run(buf, ah, al, tw, colscale);
+    }
 }
+
+// Layout of the tile that tile_fft_tc leaves: TcOut for 512-point lines (the
+// fused pass is the last), plain otherwise.
+template <int LOGN, int CX>
+using TcResult = std::conditional_t<LOGN == 9, TcOut<CX>, TcPlain<CX>>;
 
 }  // namespace kwgb

@@ -126,7 +126,7 @@ __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX,
         __syncthreads();
         tile_fft_tc<LOGN, CX, +1, THREADS, MIXED>(tile, tw, colscale);
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = S.at(j + TL * m);
+        for (int m = 0; m < E; ++m) v[m] = tile[TcResult<LOGN, CX>::idx(j + TL * m, S.c)];
     }
 }
 
@@ -205,8 +205,13 @@ yz_kernel(const __grid_constant__ YZK a) {
         float2 v[E];
         if constexpr (MIXED != 0)
             tile_fft_tc<LOGN, CX, (ISY ? (OP == OP_Y_FWD ? -1 : +1) : -1), THREADS, MIXED>(smem + s * STAGE, g.t.tw, colscale);
+        if constexpr (MIXED != 0) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = S.raw(j + TL * m);
+            for (int m = 0; m < E; ++m) v[m] = smem[s * STAGE + TcResult<LOGN, CX>::idx(j + TL * m, c)];
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = S.raw(j + TL * m);
+        }
 
         if (ISY) {
             const int comp = item / (nchunk * lines);

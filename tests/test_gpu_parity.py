@@ -193,7 +193,9 @@ MIXED = {"bf16": 4, "f16": 8}
 
 
 @pytest.mark.parametrize("form", ["bf16", "f16"])
-@pytest.mark.parametrize("shape", [(16, 16, 16), (64, 64, 64), (32, 512, 16), (512, 16, 32)])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (64, 64, 64), (32, 512, 16), (512, 16, 32),
+                                   (128, 16, 16), (16, 128, 32), (256, 16, 64), (16, 256, 64),
+                                   (1024, 16, 16), (16, 1024, 8)])
 @pytest.mark.parametrize("op", [0, 1, 2, 3])
 def test_mixed_operator_parity(kw, form, shape, op):
     import torch
