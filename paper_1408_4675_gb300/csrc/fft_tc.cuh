@@ -20,7 +20,11 @@
 // Each thread reads its B fragment (two complex inputs of one butterfly)
 // straight from the Stockham input positions, applies the stage twiddles, and
 // writes its D fragment (one complex output of two butterflies) straight to
-// the Stockham output positions, so no extra shuffles are needed.
+// the Stockham output positions, so no extra shuffles are needed.  For 512-
+// and 1024-point lines the stages of strides 8 and 64 share one pass
+// (tc_stage8x8: the accumulator fragment of the first product is the operand
+// fragment of the second).  Between passes the tile is XOR-swizzled so that
+// the accesses are free of bank conflicts (TcSwz, TcXor).
 #pragma once
 
 #include <cuda_bf16.h>

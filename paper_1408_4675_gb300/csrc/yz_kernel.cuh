@@ -132,9 +132,11 @@ __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX,
 
 // MIXED = 1 / 2: the transforms run as bfloat16- / float16-split tensor-core
 // products on the tile in shared memory (fft_tc.cuh) instead of the float32
-// register passes.
+// register passes.  Two CTAs per SM for the z passes of 512-point lines in
+// both forms (the mixed form then spills a few words of its operator values,
+// which costs less than the idle barrier time of one CTA per SM).
 template <int LOGN, int OP, int MIXED>
-__global__ void __launch_bounds__(TShape<LOGN, (OP < 2)>::THREADS, ((OP < 2) || LOGN >= 10 || MIXED) ? 1 : 2)
+__global__ void __launch_bounds__(TShape<LOGN, (OP < 2)>::THREADS, ((OP < 2) || LOGN >= 10 || (MIXED && LOGN != 9)) ? 1 : 2)
 yz_kernel(const __grid_constant__ YZK a) {
     constexpr bool ISY = OP < 2;
     using Sh = TShape<LOGN, ISY>;
