@@ -24,9 +24,9 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-template <int LOGN, bool ISY>
+template <int LOGN, bool ISY, int MIXED>
 static int encode_box(const GridC& g, float2* ptr, CUtensorMap* map) {
-    using Sh = TShape<LOGN, ISY>;
+    using Sh = TShape<LOGN, ISY, MIXED>;
     EncodeTiledFn fn = encode_fn();
     if (!fn) return -1;
     const cuuint64_t dims[3] = {(cuuint64_t)g.nh, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
@@ -44,13 +44,13 @@ int make_spec_maps(const GridC& g, float2* ptr, SpecBuf* out) {
     out->p = ptr;
     int e = -3;
     switch (g.logny) {
-#define CASE(L) case L: e = encode_box<L, true>(g, ptr, &out->ymap); break;
+#define CASE(L) case L: e = g.mixed ? encode_box<L, true, 1>(g, ptr, &out->ymap) : encode_box<L, true, 0>(g, ptr, &out->ymap); break;
         KWGB_LOG_CASES(CASE)
 #undef CASE
     }
     if (e) return e;
     switch (g.lognz) {
-#define CASE(L) case L: e = encode_box<L, false>(g, ptr, &out->zmap); break;
+#define CASE(L) case L: e = g.mixed ? encode_box<L, false, 1>(g, ptr, &out->zmap) : encode_box<L, false, 0>(g, ptr, &out->zmap); break;
         KWGB_LOG_CASES(CASE)
 #undef CASE
     }
@@ -65,10 +65,11 @@ static cudaError_t launch_op(int op, const YZK& a, int logn, int items, cudaStre
 
 static int chunk_count(int nh, int cx) { return (nh + cx - 1) / cx; }
 
+// tile width of the pass (the tensor-core forms share one shape)
 template <bool ISY>
-static int cx_of(int logn) {
+static int cx_of(int logn, int mixed) {
     switch (logn) {
-#define CASE(L) case L: return TShape<L, ISY>::CX;
+#define CASE(L) case L: return mixed ? TShape<L, ISY, 1>::CX : TShape<L, ISY, 0>::CX;
         KWGB_LOG_CASES(CASE)
 #undef CASE
     }
@@ -87,7 +88,7 @@ cudaError_t launch_y_pass(const GridC& g, int dir, const SpecBuf* const* in, flo
     a.ncomp = ncomp;
     a.nloads = 1;
     a.flag = flag;
-    const int items = chunk_count(g.nh, cx_of<true>(g.logny)) * g.nz * ncomp;
+    const int items = chunk_count(g.nh, cx_of<true>(g.logny, g.mixed)) * g.nz * ncomp;
     return launch_op(dir < 0 ? OP_Y_FWD : OP_Y_INV, a, g.logny, items, s);
 }
 
@@ -118,7 +119,7 @@ cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, floa
         a.nloads = n;
         if (n == 0) return cudaSuccess;
     }
-    const int items = chunk_count(g.nh, cx_of<false>(g.lognz)) * g.ny;
+    const int items = chunk_count(g.nh, cx_of<false>(g.lognz, g.mixed)) * g.ny;
     switch (kind) {
         case Z_GRAD_FWD: return launch_op(OP_Z_GRAD_FWD, a, g.lognz, items, s);
         case Z_GRAD_BWD: return launch_op(OP_Z_GRAD_BWD, a, g.lognz, items, s);

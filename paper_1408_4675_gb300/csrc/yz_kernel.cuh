@@ -48,14 +48,16 @@ struct TileSmem {
     __device__ __forceinline__ void sync() { __syncthreads(); }
 };
 
-template <int LOGN, bool ISY>
+// MIXED: the tensor-core forms take 8-column tiles of 256 threads for 512-point
+// y lines (64 KB per CTA: two CTAs per SM; the float32 y pass keeps 16 columns)
+template <int LOGN, bool ISY, int MIXED = 0>
 struct TShape {
     static constexpr int N = 1 << LOGN;
     // z: E = 8 keeps the operator pass spill-free at two CTAs per SM; 1024-point
     // lines take E = 16 so that a tile stays 8 columns (64-byte TMA rows) wide
     static constexpr int E = ISY ? (LOGN >= 8 ? 16 : 8) : (LOGN >= 10 ? 16 : 8);
     static constexpr int TL = N / E;
-    static constexpr int MAXT = 512;
+    static constexpr int MAXT = (ISY && MIXED && LOGN == 9) ? 256 : 512;
     static constexpr int CX = (MAXT / TL) >= 16 ? 16 : (MAXT / TL);
     static constexpr int THREADS = CX * TL;
     static constexpr int BOX = N < 256 ? N : 256;
@@ -136,10 +138,17 @@ __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX,
 // both forms (the mixed form then spills a few words of its operator values,
 // which costs less than the idle barrier time of one CTA per SM).
 template <int LOGN, int OP, int MIXED>
-__global__ void __launch_bounds__(TShape<LOGN, (OP < 2)>::THREADS, ((OP < 2) || LOGN >= 10 || (MIXED && LOGN != 9)) ? 1 : 2)
+constexpr int yz_min_blocks() {
+    if (OP < 2) return (MIXED && LOGN == 9) ? 3 : 1;
+    if (LOGN >= 10) return 1;
+    return (MIXED && LOGN != 9) ? 1 : 2;
+}
+
+template <int LOGN, int OP, int MIXED>
+__global__ void __launch_bounds__(TShape<LOGN, (OP < 2), MIXED>::THREADS, yz_min_blocks<LOGN, OP, MIXED>())
 yz_kernel(const __grid_constant__ YZK a) {
     constexpr bool ISY = OP < 2;
-    using Sh = TShape<LOGN, ISY>;
+    using Sh = TShape<LOGN, ISY, MIXED>;
     constexpr int E = Sh::E, TL = Sh::TL, CX = Sh::CX, STAGE = Sh::STAGE;
     extern __shared__ __align__(128) float2 smem[];
     __shared__ int abort_flag;
@@ -323,7 +332,7 @@ yz_kernel(const __grid_constant__ YZK a) {
 
 template <int LOGN, int OP, int MIXED>
 inline cudaError_t launch_t(const YZK& a, int items, cudaStream_t s) {
-    using Sh = TShape<LOGN, (OP < 2)>;
+    using Sh = TShape<LOGN, (OP < 2), MIXED>;
     auto k = yz_kernel<LOGN, OP, MIXED>;
     static int per_sm = 0;
     if (per_sm == 0) {
