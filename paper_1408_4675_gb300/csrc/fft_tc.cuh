@@ -180,12 +180,31 @@ using TcMid = TcXor<CX, 1u | (1u << (LOGN - 6)), 1u << (LOGN - 5), 1u << (LOGN -
 template <int CX>
 using TcOut = TcXor<CX, 1u << 4, 1u << 5, 1u << 6, CX == 16 ? (1u << 7) : 0u, CX == 8 ? (1u << 7) : 0u>;
 
+// Float16-split column scale from the bits of the column maximum m (a
+// non-negative float): 2^k with m 2^k in [32, 64), k clamped to [-100, 100]
+// (zero, subnormal-range and non-finite maxima stay finite); 2^-k when
+// `inverse`.  1 for a zero or non-finite maximum.
+__device__ __forceinline__ float col_scale(unsigned int mbits, bool inverse) {
+    const int ex = (int)((mbits >> 23) & 0xffu);               // m in [2^(ex-127), 2^(ex-126))
+    if (mbits == 0u || ex == 0xff) return 1.0f;
+    const int k = max(-100, min(100, 132 - ex));
+    return __int_as_float((127 + (inverse ? -k : k)) << 23);
+}
+
+// Column maxima of the float16-split form: two buffers of 16 words in shared
+// memory that alternate between transforms (all zero at the start); a
+// transform fills buffer `cur` and clears the other one for the next.
+struct TcColMax {
+    unsigned int* m;
+    int cur;
+};
+
 // One radix-8 Stockham stage (stride NS) of a tile, on the tensor cores.
 // Butterfly beta = 32 w + 8 G + n (column c = beta % CX, butterfly b = beta / CX).
 // LI / LO: the layouts the stage reads and writes (TcSwz, TcXor).
 template <int N, int CX, int NS, int DIR, int THREADS, int PREC, class LI, class LO>
 __device__ __forceinline__ void tc_stage8(float2* buf, const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                          const float2* __restrict__ tw, const float* colscale) {
+                                          const float2* __restrict__ tw, const unsigned int* colmax) {
     constexpr int NBF = CX * N / 8;                           // butterflies in the tile
     constexpr int WARPS = THREADS / 32;
     constexpr int GROUPS = NBF / (8 * WARPS);                 // 8-butterfly groups per warp
@@ -210,7 +229,7 @@ __device__ __forceinline__ void tc_stage8(float2* buf, const uint32_t (&ah)[4], 
             x1 = cmul(x1, twiddle1024<DIR>(tw, k * (2 * t + 1) * (1024 / (NS * 8))));
         }
         if (PREC == 2) {
-            const float sc = colscale[c];
+            const float sc = col_scale(colmax[c], false);
             x0 = cscale(x0, sc);
             x1 = cscale(x1, sc);
         }
@@ -230,7 +249,7 @@ __device__ __forceinline__ void tc_stage8(float2* buf, const uint32_t (&ah)[4], 
             const int beta = (w * GROUPS + G) * 8 + 2 * t + i;
             const int c = beta % CX, b = beta / CX;
             const int base = (b / NS) * NS * 8 + (b & (NS - 1));
-            const float us = PREC == 2 ? 1.0f / colscale[c] : 1.0f;           // exact: a power of two
+            const float us = PREC == 2 ? col_scale(colmax[c], true) : 1.0f;
             const float2 o = make_float2(d[G][i] * us, d[G][2 + i] * us);
             buf[LO::at(base + g * NS, c, LO::hcol(base) ^ hw, LO::hrow(base) ^ pw)] = o;
         }
@@ -294,7 +313,7 @@ __device__ __forceinline__ void f32_stage(float2* buf, const float2* __restrict_
 // most 64x in between, which float16 holds at the [32, 64) input scale).
 template <int N, int CX, int DIR, int THREADS, int PREC, class LI, class LO>
 __device__ __forceinline__ void tc_stage8x8(float2* buf, const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                            const float2* __restrict__ tw, const float* colscale) {
+                                            const float2* __restrict__ tw, const unsigned int* colmax) {
     static_assert(N == 512 || N == 1024, "strides 8 and 64 of a 512- or 1024-point line");
     constexpr int WARPS = THREADS / 32;
     constexpr int GROUPS = CX * (N / 64) / WARPS;            // groups per warp
@@ -321,7 +340,7 @@ __device__ __forceinline__ void tc_stage8x8(float2* buf, const uint32_t (&ah)[4]
         x0 = cmul(x0, twiddle1024<DIR>(tw, alpha * (2 * t) * 16));
         x1 = cmul(x1, twiddle1024<DIR>(tw, alpha * (2 * t + 1) * 16));
         if (PREC == 2) {
-            const float sc = colscale[c];
+            const float sc = col_scale(colmax[c], false);
             x0 = cscale(x0, sc);
             x1 = cscale(x1, sc);
         }
@@ -351,7 +370,7 @@ __device__ __forceinline__ void tc_stage8x8(float2* buf, const uint32_t (&ah)[4]
         const int c = grp % CX, B0 = grp / CX;
         const int rb = 512 * (B0 >> 3) + (B0 & 7);
         const int hb = LO::hcol(rb), pb = LO::hrow(rb);
-        const float us = PREC == 2 ? 1.0f / colscale[c] : 1.0f;               // exact: a power of two
+        const float us = PREC == 2 ? col_scale(colmax[c], true) : 1.0f;
         buf[LO::at(rb + wr0, c, hb ^ wh0, pb ^ wp0)] = make_float2(d[G][0] * us, d[G][2] * us);
         buf[LO::at(rb + wr1, c, hb ^ wh1, pb ^ wp1)] = make_float2(d[G][1] * us, d[G][3] * us);
     }
@@ -362,14 +381,14 @@ __device__ __forceinline__ void tc_stage8x8(float2* buf, const uint32_t (&ah)[4]
 template <int LOGN, int CX, int DIR, int THREADS, int PREC, int NS>
 struct TcChain {
     __device__ __forceinline__ static void run(float2* buf, const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                               const float2* __restrict__ tw, const float* colscale) {
+                                               const float2* __restrict__ tw, const unsigned int* colmax) {
         constexpr int N = 1 << LOGN;
         constexpr int REM = N / NS;
         if constexpr (REM >= 8) {
             using LI = std::conditional_t<(NS > 1), TcSwz<LOGN, CX>, TcPlain<CX>>;
             using LO = std::conditional_t<(NS * 8 < N), TcSwz<LOGN, CX>, TcPlain<CX>>;
-            tc_stage8<N, CX, NS, DIR, THREADS, PREC, LI, LO>(buf, ah, al, tw, colscale);
-            TcChain<LOGN, CX, DIR, THREADS, PREC, NS * 8>::run(buf, ah, al, tw, colscale);
+            tc_stage8<N, CX, NS, DIR, THREADS, PREC, LI, LO>(buf, ah, al, tw, colmax);
+            TcChain<LOGN, CX, DIR, THREADS, PREC, NS * 8>::run(buf, ah, al, tw, colmax);
         } else {
             using LI = std::conditional_t<(NS > 1), TcSwz<LOGN, CX>, TcPlain<CX>>;
             f32_stage<N, CX, (REM >= 4 ? 4 : 2), NS, DIR, THREADS, LI>(buf, tw);
@@ -379,24 +398,22 @@ struct TcChain {
 template <int LOGN, int CX, int DIR, int THREADS, int PREC>
 struct TcChain<LOGN, CX, DIR, THREADS, PREC, (1 << LOGN)> {
     __device__ __forceinline__ static void run(float2*, const uint32_t (&)[4], const uint32_t (&)[4],
-                                               const float2*, const float*) {}
+                                               const float2*, const unsigned int*) {}
 };
 
 // In-place unnormalised DFT of every column of the tile (natural order in and
 // out; the input in the plain layout, the result in layout TcResult).
 // Starts and ends with the tile fully written (callers synchronise before).
-// colscale: CX floats of shared memory (used by PREC 2).
+// cmx: the column maxima of the float16-split form (PREC 2).
 template <int LOGN, int CX, int DIR, int THREADS, int PREC>
-__device__ __forceinline__ void tile_fft_tc(float2* buf, const float2* __restrict__ tw, float* colscale) {
+__device__ __forceinline__ void tile_fft_tc(float2* buf, const float2* __restrict__ tw, TcColMax& cmx) {
     uint32_t ah[4], al[4];
     dft8_matrix<DIR, PREC>(threadIdx.x & 31, ah, al);
+    unsigned int* colmax = cmx.m + 16 * cmx.cur;
     if constexpr (PREC == 2) {
-        // per column: largest |Re|, |Im| -> power-of-two scale to [32, 64)
+        // per column: largest |Re|, |Im| (each stage turns it into its power-of-two scale)
         constexpr int N = 1 << LOGN;
-        static_assert(THREADS % CX == 0 && CX <= 32 && (N * CX) % THREADS == 0, "column of a thread");
-        unsigned int* cm = reinterpret_cast<unsigned int*>(colscale);
-        if (threadIdx.x < CX) cm[threadIdx.x] = 0u;
-        __syncthreads();
+        static_assert(THREADS % CX == 0 && CX <= 16 && (N * CX) % THREADS == 0, "column of a thread");
         // every element a thread visits lies in column threadIdx.x % CX: a local
         // maximum, then a butterfly over the lanes of the same column, then one
         // shared atomic per column and warp
@@ -408,24 +425,20 @@ __device__ __forceinline__ void tile_fft_tc(float2* buf, const float2* __restric
         }
 #pragma unroll
         for (int o = CX; o < 32; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) < CX) atomicMax(cm + (threadIdx.x % CX), __float_as_uint(m));   // non-negative floats order as integers
-        __syncthreads();
-        if (threadIdx.x < CX) {
-            const float m = __uint_as_float(cm[threadIdx.x]);
-            int e = 0;
-            if (m > 0.f && isfinite(m)) frexpf(m, &e);          // m = f 2^e, f in [0.5, 1)
-            colscale[threadIdx.x] = (m > 0.f && isfinite(m)) ? ldexpf(1.0f, 6 - e) : 1.0f;
-        }
+        if ((threadIdx.x & 31) < CX) atomicMax(colmax + (threadIdx.x % CX), __float_as_uint(m));   // non-negative floats order as integers
+        // the other buffer's last readers were the stages of the previous transform
+        if (threadIdx.x < CX) cmx.m[16 * (cmx.cur ^ 1) + threadIdx.x] = 0u;
         __syncthreads();
     }
+    cmx.cur ^= 1;
     if constexpr (LOGN == 9 || LOGN == 10) {
         // stride 1, then strides 8 and 64 in one pass, then (1024) a float32 radix-2 stage
         constexpr int N = 1 << LOGN;
-        tc_stage8<N, CX, 1, DIR, THREADS, PREC, TcPlain<CX>, TcMid<LOGN, CX>>(buf, ah, al, tw, colscale);
-        tc_stage8x8<N, CX, DIR, THREADS, PREC, TcMid<LOGN, CX>, TcOut<CX>>(buf, ah, al, tw, colscale);
+        tc_stage8<N, CX, 1, DIR, THREADS, PREC, TcPlain<CX>, TcMid<LOGN, CX>>(buf, ah, al, tw, colmax);
+        tc_stage8x8<N, CX, DIR, THREADS, PREC, TcMid<LOGN, CX>, TcOut<CX>>(buf, ah, al, tw, colmax);
         if constexpr (LOGN == 10) f32_stage<N, CX, 2, 512, DIR, THREADS, TcOut<CX>>(buf, tw);
     } else {
-        TcChain<LOGN, CX, DIR, THREADS, PREC, 1>::run(buf, ah, al, tw, colscale);
+        TcChain<LOGN, CX, DIR, THREADS, PREC, 1>::run(buf, ah, al, tw, colmax);
     }
 }
 

@@ -117,7 +117,7 @@ __device__ __forceinline__ float2* out_ptr(const YZK& a, int i) {
 // float32 register passes, or (MIXED) through the tile in shared memory.
 template <int LOGN, int E, int CX, int THREADS, int MIXED>
 __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX, MIXED == 0>& S, float2* tile,
-                                             const float2* __restrict__ tw, float* colscale) {
+                                             const float2* __restrict__ tw, TcColMax& cmx) {
     constexpr int TL = (1 << LOGN) / E;
     if constexpr (MIXED == 0) {
         line_fft<LOGN, E, +1>(v, j, S, tw);
@@ -126,7 +126,7 @@ __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX,
 #pragma unroll
         for (int m = 0; m < E; ++m) S.at(j + TL * m) = v[m];
         __syncthreads();
-        tile_fft_tc<LOGN, CX, +1, THREADS, MIXED>(tile, tw, colscale);
+        tile_fft_tc<LOGN, CX, +1, THREADS, MIXED>(tile, tw, cmx);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = tile[TcResult<LOGN, CX>::idx(j + TL * m, S.c)];
     }
@@ -152,7 +152,7 @@ yz_kernel(const __grid_constant__ YZK a) {
     constexpr int E = Sh::E, TL = Sh::TL, CX = Sh::CX, STAGE = Sh::STAGE;
     extern __shared__ __align__(128) float2 smem[];
     __shared__ int abort_flag;
-    __shared__ float colscale[16];                  // per-column scales of the float16-split form
+    __shared__ unsigned int colmax[32];              // column maxima of the float16-split form (2 buffers)
     float2* scratch = smem + 2 * STAGE;             // float32 exchanges (not used by MIXED)
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (MIXED ? 2 : 3) * STAGE);
     const GridC& g = a.g;
@@ -174,6 +174,8 @@ yz_kernel(const __grid_constant__ YZK a) {
         fence_mbar_init();
         abort_flag = 0;
     }
+    if (tid < 32) colmax[tid] = 0u;
+    TcColMax cmx{colmax, 0};
     __syncthreads();
 
     auto issue = [&](int q) {                 // thread 0 only
@@ -215,7 +217,7 @@ yz_kernel(const __grid_constant__ YZK a) {
         constexpr int THREADS = Sh::THREADS;
         float2 v[E];
         if constexpr (MIXED != 0)
-            tile_fft_tc<LOGN, CX, (ISY ? (OP == OP_Y_FWD ? -1 : +1) : -1), THREADS, MIXED>(smem + s * STAGE, g.t.tw, colscale);
+            tile_fft_tc<LOGN, CX, (ISY ? (OP == OP_Y_FWD ? -1 : +1) : -1), THREADS, MIXED>(smem + s * STAGE, g.t.tw, cmx);
         if constexpr (MIXED != 0) {
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = smem[s * STAGE + TcResult<LOGN, CX>::idx(j + TL * m, c)];
@@ -272,7 +274,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                 float2* o1 = a.out[1];
                 float2* o2 = a.out[2];
                 if (o0 != nullptr || o1 != nullptr) {           // uniform
-                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, colscale);
+                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, cmx);
                     if (valid) {
 #pragma unroll
                         for (int m = 0; m < E; ++m) {
@@ -283,7 +285,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                     }
                 }
                 if (o2 != nullptr) {
-                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(w, j, S, smem + s * STAGE, g.t.tw, colscale);
+                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(w, j, S, smem + s * STAGE, g.t.tw, cmx);
                     if (valid) {
 #pragma unroll
                         for (int m = 0; m < E; ++m) __stcs(o2 + off + (size_t)(j + TL * m) * es, w[m]);
@@ -299,7 +301,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                     if (OP == OP_Z_DIV) d = make_float2(-d.x, d.y);   // Eq. 4c: i k e^{-ikd/2}
                     v[m] = cscale(cmul(v[m], d), kap[m]);            // OP_Z_DIV_FWD: Eq. 4a's operator
                 }
-                inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, colscale);
+                inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, cmx);
                 if (valid) {
                     float2* out = out_ptr(a, xi) + off;
 #pragma unroll
@@ -313,7 +315,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                     const float f = lg[m] > -INFINITY ? exp2f(e * lg[m]) * cst : 0.f;   // k^{y-2} / k^{y-1}, 0 at k = 0
                     v[m] = cscale(v[m], f);
                 }
-                inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, colscale);
+                inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, cmx);
                 if (valid) {
                     float2* out = out_ptr(a, t) + off;
 #pragma unroll
