@@ -181,14 +181,14 @@ template <int CX>
 using TcOut = TcXor<CX, 1u << 4, 1u << 5, 1u << 6, CX == 16 ? (1u << 7) : 0u, CX == 8 ? (1u << 7) : 0u>;
 
 // Float16-split column scale from the bits of the column maximum m (a
-// non-negative float): 2^k with m 2^k in [32, 64), k clamped to [-100, 100]
-// (zero, subnormal-range and non-finite maxima stay finite); 2^-k when
-// `inverse`.  1 for a zero or non-finite maximum.
+// non-negative float, biased exponent ex): 2^k with k = 132 - ex, so that
+// m 2^k lies in [32, 64), or 2^-k when `inverse`; k is clamped to [-100, 100]
+// (a zero column takes 2^100, a non-finite one 2^-100: both stay what they
+// are).  Branch-free: the result's biased exponent is 127 +- k.
 __device__ __forceinline__ float col_scale(unsigned int mbits, bool inverse) {
-    const int ex = (int)((mbits >> 23) & 0xffu);               // m in [2^(ex-127), 2^(ex-126))
-    if (mbits == 0u || ex == 0xff) return 1.0f;
-    const int k = max(-100, min(100, 132 - ex));
-    return __int_as_float((127 + (inverse ? -k : k)) << 23);
+    const int ex = (int)(mbits >> 23);                           // sign bit clear
+    const int be = inverse ? ex - 5 : 259 - ex;
+    return __int_as_float(max(27, min(227, be)) << 23);
 }
 
 // Column maxima of the float16-split form: two buffers of 16 words in shared
@@ -339,8 +339,9 @@ __device__ __forceinline__ void tc_stage8x8(float2* buf, const uint32_t (&ah)[4]
         // stage a: input m of a butterfly with b % 8 = alpha times exp(DIR 2 pi i alpha m / 64)
         x0 = cmul(x0, twiddle1024<DIR>(tw, alpha * (2 * t) * 16));
         x1 = cmul(x1, twiddle1024<DIR>(tw, alpha * (2 * t + 1) * 16));
+        const unsigned int cmb = PREC == 2 ? colmax[c] : 0u;   // one tile column per group
         if (PREC == 2) {
-            const float sc = col_scale(colmax[c], false);
+            const float sc = col_scale(cmb, false);
             x0 = cscale(x0, sc);
             x1 = cscale(x1, sc);
         }
@@ -362,6 +363,11 @@ __device__ __forceinline__ void tc_stage8x8(float2* buf, const uint32_t (&ah)[4]
         mma_16816<PREC>(d[G], al, bh0, bh1);
         mma_16816<PREC>(d[G], ah, bl0, bl1);
         mma_16816<PREC>(d[G], ah, bh0, bh1);
+        if (PREC == 2) {
+            const float us = col_scale(cmb, true);                // exact: a power of two
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[G][k] *= us;
+        }
     }
     __syncthreads();                                          // all inputs read
 #pragma unroll
@@ -370,9 +376,8 @@ __device__ __forceinline__ void tc_stage8x8(float2* buf, const uint32_t (&ah)[4]
         const int c = grp % CX, B0 = grp / CX;
         const int rb = 512 * (B0 >> 3) + (B0 & 7);
         const int hb = LO::hcol(rb), pb = LO::hrow(rb);
-        const float us = PREC == 2 ? col_scale(colmax[c], true) : 1.0f;
-        buf[LO::at(rb + wr0, c, hb ^ wh0, pb ^ wp0)] = make_float2(d[G][0] * us, d[G][2] * us);
-        buf[LO::at(rb + wr1, c, hb ^ wh1, pb ^ wp1)] = make_float2(d[G][1] * us, d[G][3] * us);
+        buf[LO::at(rb + wr0, c, hb ^ wh0, pb ^ wp0)] = make_float2(d[G][0], d[G][2]);
+        buf[LO::at(rb + wr1, c, hb ^ wh1, pb ^ wp1)] = make_float2(d[G][1], d[G][3]);
     }
     __syncthreads();
 }
