@@ -406,33 +406,41 @@ struct TcChain<LOGN, CX, DIR, THREADS, PREC, (1 << LOGN)> {
                                                const float2*, const unsigned int*) {}
 };
 
+// Float16-split: a thread's maximum m of the column threadIdx.x % CX goes into
+// the current buffer of cmx (a butterfly over the lanes of the same column, one
+// shared atomic per column and warp), and the other buffer is cleared for the
+// next transform (its last readers were the stages of the previous one).
+template <int CX>
+__device__ __forceinline__ void tc_colmax_deposit(float m, TcColMax& cmx) {
+#pragma unroll
+    for (int o = CX; o < 32; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) < CX) atomicMax(cmx.m + 16 * cmx.cur + (threadIdx.x % CX), __float_as_uint(m));   // non-negative floats order as integers
+    if (threadIdx.x < CX) cmx.m[16 * (cmx.cur ^ 1) + threadIdx.x] = 0u;
+}
+
 // In-place unnormalised DFT of every column of the tile (natural order in and
 // out; the input in the plain layout, the result in layout TcResult).
 // Starts and ends with the tile fully written (callers synchronise before).
-// cmx: the column maxima of the float16-split form (PREC 2).
-template <int LOGN, int CX, int DIR, int THREADS, int PREC>
+// cmx: the column maxima of the float16-split form (PREC 2).  SCAN: the
+// transform reads the tile for them; otherwise every thread has already
+// deposited them (tc_colmax_deposit) before the caller's barrier.
+template <int LOGN, int CX, int DIR, int THREADS, int PREC, bool SCAN = true>
 __device__ __forceinline__ void tile_fft_tc(float2* buf, const float2* __restrict__ tw, TcColMax& cmx) {
     uint32_t ah[4], al[4];
     dft8_matrix<DIR, PREC>(threadIdx.x & 31, ah, al);
     unsigned int* colmax = cmx.m + 16 * cmx.cur;
-    if constexpr (PREC == 2) {
+    if constexpr (PREC == 2 && SCAN) {
         // per column: largest |Re|, |Im| (each stage turns it into its power-of-two scale)
         constexpr int N = 1 << LOGN;
         static_assert(THREADS % CX == 0 && CX <= 16 && (N * CX) % THREADS == 0, "column of a thread");
-        // every element a thread visits lies in column threadIdx.x % CX: a local
-        // maximum, then a butterfly over the lanes of the same column, then one
-        // shared atomic per column and warp
+        // every element a thread visits lies in column threadIdx.x % CX
         float m = 0.f;
 #pragma unroll 4
         for (int i = threadIdx.x; i < N * CX; i += THREADS) {
             const float2 v = buf[i];
             m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
-#pragma unroll
-        for (int o = CX; o < 32; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) < CX) atomicMax(colmax + (threadIdx.x % CX), __float_as_uint(m));   // non-negative floats order as integers
-        // the other buffer's last readers were the stages of the previous transform
-        if (threadIdx.x < CX) cmx.m[16 * (cmx.cur ^ 1) + threadIdx.x] = 0u;
+        tc_colmax_deposit<CX>(m, cmx);
         __syncthreads();
     }
     cmx.cur ^= 1;

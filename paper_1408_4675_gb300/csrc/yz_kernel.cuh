@@ -125,8 +125,14 @@ __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX,
         __syncthreads();                              // every thread is done reading the tile
 #pragma unroll
         for (int m = 0; m < E; ++m) S.at(j + TL * m) = v[m];
+        if constexpr (MIXED == 2) {                   // column maxima from the registers: no tile scan
+            float mx = 0.f;
+#pragma unroll
+            for (int m = 0; m < E; ++m) mx = fmaxf(mx, fmaxf(fabsf(v[m].x), fabsf(v[m].y)));
+            tc_colmax_deposit<CX>(mx, cmx);
+        }
         __syncthreads();
-        tile_fft_tc<LOGN, CX, +1, THREADS, MIXED>(tile, tw, cmx);
+        tile_fft_tc<LOGN, CX, +1, THREADS, MIXED, false>(tile, tw, cmx);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = tile[TcResult<LOGN, CX>::idx(j + TL * m, S.c)];
     }
