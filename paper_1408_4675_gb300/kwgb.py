@@ -20,6 +20,7 @@ ERRORS = {-1: "ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: 
           -7: "UNSUPPORTED"}
 
 NONLINEAR, ABSORBING = 1, 2
+MIXED_BF16, MIXED_F16 = 4, 8          # split-precision tensor-core y/z FFT stages (KWGB_MIXED_*)
 P_MAX, P_RMS, I_AVG, P_MIN, P_SERIES, U_SERIES = 1, 2, 4, 8, 16, 32
 ADDITIVE_MASS = 0
 FORCE_X, FORCE_Y, FORCE_Z = 1, 2, 3

@@ -139,3 +139,27 @@ def test_product_package_does_not_reach_the_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, fn)).read()
                 assert not pat.search(src), os.path.join(dirpath, fn)
+
+
+def header_constants():
+    src = open(os.path.join(ROOT, "include", "kwgb.h")).read()
+    out = {}
+    for name, val in re.findall(r"#define\s+KWGB_([A-Z0-9_]+)\s+(-?(?:0x[0-9a-fA-F]+|\d+))u?\b", src):
+        out[name] = int(val, 0)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """Every flag, record, source mode, field and operator code of the Python
+    binding has the value the C header defines."""
+    h = header_constants()
+    for name in ("NONLINEAR", "ABSORBING", "MIXED_BF16", "MIXED_F16", "P_MAX", "P_RMS", "I_AVG", "P_MIN",
+                 "P_SERIES", "U_SERIES", "ADDITIVE_MASS", "FORCE_X", "FORCE_Y", "FORCE_Z", "DIRICHLET_P",
+                 "SCALAR_C0", "SCALAR_RHO0", "SCALAR_BONA", "SCALAR_ALPHA0", "INPUT_DEVICE", "FIELD_P",
+                 "FIELD_UX", "FIELD_UY", "FIELD_UZ", "FIELD_RHOX", "FIELD_RHOY", "FIELD_RHOZ", "OP_GRAD_FWD",
+                 "OP_GRAD_BWD", "OP_ABS_TAU", "OP_ABS_ETA"):
+        assert name in h, name
+        assert getattr(kwgb, name) == h[name], (name, getattr(kwgb, name), h[name])
+    assert kwgb.KWGB_OK == h["OK"]
+    for code, short in kwgb.ERRORS.items():
+        assert h["ERR_" + short] == code, short
