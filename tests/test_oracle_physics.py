@@ -1,8 +1,10 @@
 """Physics pins of the FP64 oracle: the nonlinear coefficient beta = 1 + B/2A
 that Eq. 2 implies (Fubini's pre-shock harmonics of a plane wave), the
 emitted amplitudes of the additive mass source, the force source and the
-Dirichlet pressure source, and a PML sanity check (the paper gives no PML
-profile, so the PML itself stays unpinned)."""
+Dirichlet pressure source, the attenuation and phase speed of a driven plane
+wave in an absorbing medium against the dispersion relation of the model, and
+a PML sanity check (the paper gives no PML profile, so the PML itself stays
+unpinned)."""
 
 import math
 
@@ -177,3 +179,63 @@ def test_dirichlet_source_holds_and_radiates_its_value():
     held = sim.p[z_src, 1, 1]
     sim.step(steps - nt)
     assert sim.p[z_src, 1, 1] != held and abs(sim.p[z_src, 1, 1]) < 2e5
+
+
+def _dispersion_root(y, a0, omega):
+    """Complex wavenumber of a plane wave of real frequency omega in the
+    homogeneous linear absorbing medium of Eqs. 4a-4d, 6 and 8 (continuous
+    form).  With rho, p ~ exp(i (k z - omega t)): d/dt -> -i omega, the
+    operators k^(y-2), k^(y-1) act on the real part kr of k, and Eq. 6 with
+    Eq. 8 gives p = c0^2 rho (1 + i omega tau kr^(y-2) - eta kr^(y-1)); the
+    mass and momentum equations give omega^2 rho = k^2 p, so
+    k = (omega / c0) (1 + i omega tau kr^(y-2) - eta kr^(y-1))^(-1/2),
+    solved for kr by fixed-point iteration.  To first order in
+    eps = 2 a0 c0 omega^(y-1): Im k = a0 omega^y (the power law of Eq. 3)."""
+    tau = -2 * a0 * C0 ** (y - 1)
+    eta = 2 * a0 * C0 ** y * math.tan(math.pi * y / 2)
+    kr = omega / C0
+    for _ in range(200):
+        k = (omega / C0) / np.sqrt(1 + 1j * omega * tau * kr ** (y - 2) - eta * kr ** (y - 1))
+        kr = k.real
+    return k
+
+
+@pytest.mark.parametrize("y", [1.1, 1.5])
+def test_driven_plane_wave_attenuation_and_phase_speed(y):
+    """A 1 MHz plane wave driven from a planar source into a long absorbing
+    medium (4 x 4 x 512 grid, PML on z only, 40 Np/m at the source frequency):
+    at steady state its amplitude decays along z at Im k and its phase advances
+    at Re k of the dispersion relation above.  The phase speed pins the
+    dispersion term (eta, with the sign of tan(pi y / 2)), the decay the
+    absorption term (tau).  At y = 1.1 the power law a0 omega^y holds only to
+    first order: Im k is 0.89 of it, Re k puts the phase speed 6 % above c0."""
+    omega, alpha = 2 * np.pi * F0, 40.0
+    a0 = alpha / omega ** y
+    nz, z_src, steps = 512, 20, 2300
+    g = oracle.Grid(4, 4, nz, DZ, DZ, DZ, DT, C0, pml_size=(0, 0, 10), pml_alpha=(0, 0, 2.0),
+                    flags=oracle.ABSORBING, alpha_power=y)
+    sim = oracle.Simulation(g)
+    sim.set_medium(C0, RHO0, 0.0, a0)
+    t = (np.arange(steps) + 0.5) * DT
+    ramp = np.clip(t * F0 / 3, 0, 1)
+    ramp = 0.5 - 0.5 * np.cos(np.pi * ramp)
+    yy, xx = np.meshgrid(np.arange(4), np.arange(4), indexing="ij")
+    sim.add_source((xx + 4 * (yy + 4 * z_src)).ravel(), ramp * np.sin(omega * t))
+    probes = np.arange(60, 461, 5)          # 2 mm past the source to 2 mm before the PML
+    rec = []
+    for n in range(steps):
+        sim.step(1)
+        if n >= steps - 200:                # the last two periods (100 steps each)
+            rec.append(sim.p[probes, 1, 1].copy())
+    rec = np.array(rec)
+    amp = 2 * (rec * np.exp(-2j * np.pi * np.arange(200) / 100)[:, None]).sum(0) / 200
+    z = probes * DZ
+    decay = -np.polyfit(z, np.log(np.abs(amp)), 1)[0]
+    kr = abs(np.polyfit(z, np.unwrap(np.angle(amp)), 1)[0])
+    k = _dispersion_root(y, a0, omega)
+    assert abs(decay / k.imag - 1) <= 0.015, (decay, k.imag)
+    assert abs(kr / k.real - 1) <= 0.002, (kr, k.real)
+    # the root reduces to the power law a0 omega^y of Eq. 3 as the absorption vanishes
+    k_weak = _dispersion_root(y, a0 * 1e-3, omega)
+    assert abs(k_weak.imag / (a0 * 1e-3 * omega ** y) - 1) <= 1e-2
+    assert abs(k_weak.real / (omega / C0) - 1) <= 1e-3
