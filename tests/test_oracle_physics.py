@@ -2,8 +2,9 @@
 that Eq. 2 implies (Fubini's pre-shock harmonics of a plane wave), the
 emitted amplitudes of the additive mass source, the force source and the
 Dirichlet pressure source, the attenuation and phase speed of a driven plane
-wave in an absorbing medium against the dispersion relation of the model, and
-a PML sanity check (the paper gives no PML profile, so the PML itself stays
+wave in an absorbing medium against the dispersion relation of the model, the
+transmission and reflection of a plane wave at a planar interface, and a PML
+sanity check (the paper gives no PML profile, so the PML itself stays
 unpinned)."""
 
 import math
@@ -239,3 +240,44 @@ def test_driven_plane_wave_attenuation_and_phase_speed(y):
     k_weak = _dispersion_root(y, a0 * 1e-3, omega)
     assert abs(k_weak.imag / (a0 * 1e-3 * omega ** y) - 1) <= 1e-2
     assert abs(k_weak.real / (omega / C0) - 1) <= 1e-3
+
+
+@pytest.mark.parametrize("c1,r1,c2,r2", [(1500.0, 1000.0, 1800.0, 1200.0), (1800.0, 1200.0, 1500.0, 1000.0)])
+def test_plane_interface_transmission_and_reflection(c1, r1, c2, r2):
+    """Heterogeneous medium (R8's staggered density included): a 1 MHz plane
+    wave of amplitude 1 (R10) from a planar source in medium 1 meets a planar
+    interface to medium 2 at normal incidence.  The transmitted amplitude is
+    2 Z2 / (Z1 + Z2), and on the source side the incident and reflected waves
+    form a standing wave whose envelope swings between 1 + |R| and 1 - |R|,
+    R = (Z2 - Z1) / (Z2 + Z1), Z = rho0 c0 (normal-incidence pressure
+    coefficients of textbook acoustics).  Grid 4 x 4 x 512, 0.05 mm (30 and 36
+    points per wavelength), PML on z only, linear and lossless."""
+    nz, z_src, z_if, steps = 512, 20, 200, 2800
+    dt = 1.0 / F0 / 120
+    omega = 2 * np.pi * F0
+    g = oracle.Grid(4, 4, nz, DZ, DZ, DZ, dt, max(c1, c2), pml_size=(0, 0, 10), pml_alpha=(0, 0, 2.0))
+    c0 = np.full(g.shape, c1)
+    c0[z_if:] = c2
+    rho0 = np.full(g.shape, r1)
+    rho0[z_if:] = r2
+    sim = oracle.Simulation(g)
+    sim.set_medium(c0, rho0, 0.0, 0.0)
+    t = (np.arange(steps) + 0.5) * dt
+    ramp = np.clip(t * F0 / 3, 0, 1)
+    ramp = 0.5 - 0.5 * np.cos(np.pi * ramp)
+    yy, xx = np.meshgrid(np.arange(4), np.arange(4), indexing="ij")
+    sim.add_source((xx + 4 * (yy + 4 * z_src)).ravel(), ramp * np.sin(omega * t))
+    rec = []
+    for n in range(steps):
+        sim.step(1)
+        if n >= steps - 240:                # the last two periods (120 steps each)
+            rec.append(sim.p[:, 1, 1].copy())
+    rec = np.array(rec)
+    amp = np.abs(2 * (rec * np.exp(-2j * np.pi * np.arange(240) / 120)[:, None]).sum(0) / 240)
+    z1, z2 = c1 * r1, c2 * r2
+    refl, trans = (z2 - z1) / (z2 + z1), 2 * z2 / (z1 + z2)
+    transmitted = amp[z_if + 40: nz - 50]
+    incident_side = amp[z_src + 10: z_if - 10]
+    assert np.abs(transmitted / trans - 1).max() <= 5e-3, (transmitted.min(), transmitted.max(), trans)
+    assert abs(incident_side.max() / (1 + abs(refl)) - 1) <= 1e-2, (incident_side.max(), 1 + abs(refl))
+    assert abs(incident_side.min() / (1 - abs(refl)) - 1) <= 1e-2, (incident_side.min(), 1 - abs(refl))
