@@ -323,3 +323,43 @@ def test_graph_replay_equals_direct_launches(kw):
     assert a.launch_count == b.launch_count
     a.close()
     b.close()
+
+
+def _plane_wave_cfg(kw, n_steps, absorbing, interface):
+    """8 x 8 x 256 grid, 0.05 mm, PML on z only, a 1 MHz ramped sinusoid on the
+    plane z = 20 (additive mass source), full-grid p_max and p_rms: either an
+    absorbing medium (y = 1.1, 40 Np/m at 1 MHz) or a lossless medium with a
+    planar interface at z = 100 (1500 m/s, 1000 kg/m^3 | 1800 m/s, 1200 kg/m^3)."""
+    nz, ny, nx, d, f0 = 256, 8, 8, 5e-5, 1e6
+    c_ref = 1800.0 if interface else 1500.0
+    dt = 1.0 / f0 / 120 if interface else 1e-8
+    y = 1.1
+    c0 = np.full((nz, ny, nx), 1500.0, np.float32)
+    rho0 = np.full((nz, ny, nx), 1000.0, np.float32)
+    if interface:
+        c0[100:] = 1800.0
+        rho0[100:] = 1200.0
+    t = (np.arange(n_steps) + 0.5) * dt
+    ramp = np.clip(t * f0 / 3, 0, 1)
+    ramp = 0.5 - 0.5 * np.cos(np.pi * ramp)
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    plane = (xx + nx * (yy + ny * 20)).ravel()
+    return {"shape": (nz, ny, nx), "d": (d, d, d), "dt": dt, "c_ref": c_ref, "pml_size": (0, 0, 10),
+            "pml_alpha": (0.0, 0.0, 2.0), "flags": kw.ABSORBING if absorbing else 0, "alpha_power": y,
+            "c0": c0, "rho0": rho0, "bona": 0.0,
+            "alpha0": 40.0 / (2 * np.pi * f0) ** y if absorbing else 0.0, "p0": None,
+            "sources": [(plane, (1e5 * ramp * np.sin(2 * np.pi * f0 * t)).astype(np.float32))],
+            "sensors": [(None, kw_P_MAX | kw_P_RMS)], "n_steps": n_steps}
+
+
+@pytest.mark.parametrize("absorbing,interface,steps", [(True, False, 1200), (False, True, 1400)])
+def test_long_plane_wave_runs_match_oracle(kw, absorbing, interface, steps):
+    """Long horizons (1200-1400 steps, the wave crosses the grid and reaches
+    steady state): the driven plane wave of the oracle's dispersion pin in an
+    absorbing medium, and the two-media interface of its transmission pin."""
+    cfg = _plane_wave_cfg(kw, steps, absorbing, interface)
+    gsim, gids, osim, oids = _run_both(kw, cfg, steps)
+    _check_outputs(gsim, gids, osim, oids, cfg, 1e-3, 5e-3)
+    _check_fields(gsim, osim, 1e-3, 5e-3, names=("p", "uz", "rhoz"))
+    assert gsim.status() == 0
+    gsim.close()
