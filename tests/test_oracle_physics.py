@@ -2,8 +2,9 @@
 that Eq. 2 implies (Fubini's pre-shock harmonics of a plane wave), the
 emitted amplitudes of the additive mass source, the force source and the
 Dirichlet pressure source, the attenuation and phase speed of a driven plane
-wave in an absorbing medium against the dispersion relation of the model, the
-transmission and reflection of a plane wave at a planar interface, and a PML
+wave in an absorbing medium and in an absorbing layer against the dispersion
+relation of the model, the transmission and reflection of a plane wave at a
+planar interface, and a PML
 sanity check (the paper gives no PML profile, so the PML itself stays
 unpinned)."""
 
@@ -281,3 +282,48 @@ def test_plane_interface_transmission_and_reflection(c1, r1, c2, r2):
     assert np.abs(transmitted / trans - 1).max() <= 5e-3, (transmitted.min(), transmitted.max(), trans)
     assert abs(incident_side.max() / (1 + abs(refl)) - 1) <= 1e-2, (incident_side.max(), 1 + abs(refl))
     assert abs(incident_side.min() / (1 - abs(refl)) - 1) <= 1e-2, (incident_side.min(), 1 - abs(refl))
+
+
+@pytest.mark.parametrize("y", [1.1, 1.5])
+def test_absorbing_half_space(y):
+    """Heterogeneous absorption (tau and eta of Eq. 3 as fields): the driven
+    1 MHz plane wave of the dispersion pin crosses from a lossless layer into
+    an absorbing one (alpha0 nonzero for z >= 150, 40 Np/m at 1 MHz).  In the
+    absorbing layer it decays at Im k2 and advances at Re k2 of that medium's
+    dispersion root.  On the lossless side the wave reflected at the change of
+    impedance gives a standing-wave envelope of half-width |R| with
+    R = (k0 - k2) / (k0 + k2), k0 = omega / c0 (plane-wave impedance
+    rho0 omega / k)."""
+    omega, alpha = 2 * np.pi * F0, 40.0
+    a0 = alpha / omega ** y
+    nz, z_src, z_if, steps = 512, 20, 150, 2300
+    g = oracle.Grid(4, 4, nz, DZ, DZ, DZ, DT, C0, pml_size=(0, 0, 10), pml_alpha=(0, 0, 2.0),
+                    flags=oracle.ABSORBING, alpha_power=y)
+    alpha0 = np.zeros(g.shape)
+    alpha0[z_if:] = a0
+    sim = oracle.Simulation(g)
+    sim.set_medium(C0, RHO0, 0.0, alpha0)
+    t = (np.arange(steps) + 0.5) * DT
+    ramp = np.clip(t * F0 / 3, 0, 1)
+    ramp = 0.5 - 0.5 * np.cos(np.pi * ramp)
+    yy, xx = np.meshgrid(np.arange(4), np.arange(4), indexing="ij")
+    sim.add_source((xx + 4 * (yy + 4 * z_src)).ravel(), ramp * np.sin(omega * t))
+    rec = []
+    for n in range(steps):
+        sim.step(1)
+        if n >= steps - 200:
+            rec.append(sim.p[:, 1, 1].copy())
+    rec = np.array(rec)
+    amp = 2 * (rec * np.exp(-2j * np.pi * np.arange(200) / 100)[:, None]).sum(0) / 200
+    k2 = _dispersion_root(y, a0, omega)
+    probes = np.arange(z_if + 50, 461, 5)   # 2.5 mm into the absorbing layer to 2 mm before the PML
+    z = probes * DZ
+    decay = -np.polyfit(z, np.log(np.abs(amp[probes])), 1)[0]
+    kr = abs(np.polyfit(z, np.unwrap(np.angle(amp[probes])), 1)[0])
+    assert abs(decay / k2.imag - 1) <= 0.015, (decay, k2.imag)
+    assert abs(kr / k2.real - 1) <= 0.002, (kr, k2.real)
+    k0 = omega / C0
+    refl = abs((k0 - k2) / (k0 + k2))
+    envelope = np.abs(amp[z_src + 20: z_if - 10])
+    half_width = (envelope.max() - envelope.min()) / 2
+    assert abs(half_width - refl) <= 0.1 * refl + 5e-4, (half_width, refl)
