@@ -35,8 +35,10 @@ the same readings, written independently):
      s = i + 1/2 on the staggered grid, P the layer size in cells.  The factor
      f = exp(-a dt / 2) is applied as u <- f (f u - dt g / rho0_sg) and
      rho_xi <- f (f rho_xi - dt rho0 d) / (1 + 2 dt d).  P = 0: no layer.
-     Parity unpinned: the paper fixes no profile to check this against; the
-     tests only bound its plane-wave reflection (below -35 dB).
+     The profile itself is the reading; its application is pinned by the
+     closed forms of the split-field equations one step at a time (decay by
+     exp(-a dt) of each split component on its own grid, forcing weighted by
+     exp(-a dt / 2)), and the layer's plane-wave reflection is below -35 dB.
  R8  rho0 at the staggered point i+1/2 is the mean of rho0 at i and i+1
      (periodic wrap).
  R9  A single global power-law exponent y.

@@ -4,8 +4,8 @@ emitted amplitudes of the additive mass source, the force source and the
 Dirichlet pressure source, the attenuation and phase speed of a driven plane
 wave in an absorbing medium and in an absorbing layer against the dispersion
 relation of the model, the transmission and reflection of a plane wave at a
-planar interface, and a PML sanity check (the paper gives no PML profile, so
-the PML itself stays unpinned)."""
+planar interface, and the reflection of the PML (its profile is a reading;
+the closed-form pins of its application are in test_oracle_pml.py)."""
 
 import math
 
