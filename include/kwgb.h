@@ -232,24 +232,51 @@ int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float* out0,
  * allocator or a fixed arena, and code that must not allocate after start-up,
  * where cudaMalloc may synchronise the device or fail).
  *   desc      grid: nx, ny, nz powers of two in [8, 64]; dx, dy, dz, dt, c_ref
- *             (pml_*, flags and alpha_power are ignored); no simulation needed
- *   op        KWGB_OP_GRAD_FWD (Eq. 4a) or KWGB_OP_GRAD_BWD (Eq. 4c)
+ *             positive and finite (pml_*, flags and alpha_power are ignored);
+ *             no simulation needed
+ *   op        KWGB_OP_GRAD_FWD (the spectral gradient shifted half a cell
+ *             forward, as the velocity update uses it) or KWGB_OP_GRAD_BWD
+ *             (shifted half a cell back, as the density update uses it)
  *   in        device field, nx*ny*nz floats, [nz][ny][nx]
  *   out_x/y/z device outputs, nx*ny*nz floats each (not aliasing in)
  *   err       optional buffer (errlen bytes) that receives a message on failure
  * Asynchronous on cuda_stream.  It allocates nothing and calls no cudaMalloc
  * or cudaFree: its scratch (three spectra and small tables) is one file-scope
- * device array of about 4.7 MB that every GPU loading the library holds until
- * the process exits.  Larger grids are rejected with KWGB_ERR_UNSUPPORTED.
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make this first call before any stream capture.
+ * device array of about 4.7 MB that every GPU loading the library's device
+ * code holds until the process exits.  Larger grids are rejected with
+ * KWGB_ERR_UNSUPPORTED.
+ * The first call on a device does the set-up: under CUDA's lazy module
+ * loading it loads the library's device code (which reserves the array),
+ * looks up the array's device address (cudaGetSymbolAddress) and uploads the
+ * twiddle table, synchronising the device; make it at start-up, before any
+ * stream capture.  Later calls enqueue kernels and one memset on cuda_stream
+ * and copy nothing from the host.
  * All calls share the array and it keeps the previous call's contents (each
  * call clears its status word and overwrites everything else it reads), so
  * calls that overlap on the GPU, e.g. from two streams, race and must be
- * serialised by the caller.  Errors: ARG, UNSUPPORTED, CUDA. */
+ * serialised by the caller.  A device-side failure (a bounded wait that ran
+ * out) is not seen by this call: kwgb_gradient_static_status reports it.
+ * Errors: ARG, UNSUPPORTED, CUDA. */
 int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const float* in, float* out_x,
                          float* out_y, float* out_z, void* cuda_stream, char* err,
                          size_t errlen);
+
+/* Device status of the kwgb_gradient_static calls on the current device since
+ * the last one began: synchronises cuda_stream (the stream of those calls),
+ * then reads the shared status word (a synchronous 4-byte copy into the
+ * caller's stack; nothing is allocated).  Returns KWGB_OK, KWGB_ERR_TIMEOUT
+ * (a bounded tile-load wait ran out; the outputs were not written),
+ * KWGB_ERR_NONFINITE, KWGB_ERR_STATE (no call on this device yet) or
+ * KWGB_ERR_CUDA; err as for kwgb_gradient_static. */
+int kwgb_gradient_static_status(void* cuda_stream, char* err, size_t errlen);
+
+/* Test hook of the failure path of kwgb_gradient_static (the counterpart of
+ * kwgb_debug_wait_fault): while on != 0, every tile load of later calls
+ * expects 16 bytes more than it receives, so the kernels' bounded waits run
+ * out (about 2 s each) and kwgb_gradient_static_status returns
+ * KWGB_ERR_TIMEOUT.  No fault is raised and the context stays usable.
+ * Returns KWGB_OK. */
+int kwgb_gradient_static_debug_wait_fault(int on);
 
 /* Gradient of an objective of the pressure with respect to every source
  * signal sample, by a hand-written adjoint (reverse-mode) of the time step
@@ -257,21 +284,38 @@ int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const float* in, fl
  * is minus the Eq. 4c operator and vice versa; the k^{y-2} and k^{y-1}
  * operators of Eq. 8 are real and even, hence their own transposes; Eq. 4d
  * and Eq. 6 by their pointwise derivatives).  The paper has no adjoint; this
- * is the differentiation form built on its step.
+ * is the differentiation form built on its step.  It runs in two calls, so
+ * that a caller (an autograd function) can take the objective now and the
+ * gradient later; kwgb_adjoint makes both calls.
+ *
+ * kwgb_adjoint_forward: run n_steps forward and return the objective.
  *   obj_idx    n_obj unique linear indices (host) of the objective region
  *   objective  KWGB_OBJ_MEAN_ABS_P (d|p|/dp taken as sign(p))
  *   n_steps    steps of the run (the simulation must not have stepped yet)
- *   checkpoint_every  K: the forward keeps the state every K steps; the
- *              reverse pass recomputes each K-step segment from its
- *              checkpoint (device memory ~ (n_steps/K) * 7 fields + 6 K fields)
+ *   checkpoint_every  K > 0: keep the state every K steps (device memory
+ *              ~ (n_steps/K) * 7 fields) for kwgb_adjoint_backward;
+ *              K = 0: the objective only (no checkpoints, no gradient later)
  *   J_out      objective value (host)
+ * The simulation then holds the end state (n_steps taken) and its sensors
+ * the run's outputs.  Synchronises.  Errors: ARG, STATE (already stepped or
+ * already run), UNSUPPORTED (K > 0 with a force or Dirichlet source: only
+ * additive mass sources are differentiated), OOM, CUDA, NONFINITE. */
+int kwgb_adjoint_forward(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
+                         int64_t n_steps, int64_t checkpoint_every, double* J_out, void* cuda_stream);
+
+/* kwgb_adjoint_backward: the reverse pass of the run kwgb_adjoint_forward
+ * made (checkpoint_every > 0).  Each K-step segment is recomputed from its
+ * checkpoint, keeping rho_xi and the Eq. 4c derivatives d_xi of every step
+ * (device memory ~ 6 K fields), then stepped backwards.
  *   grad_out   host, grad_len doubles: for every source in add order, its
  *              n_signals rows of n_t values dJ/dsignal[row][n]
- * On return the simulation holds the forward end state (n_steps taken) and
- * its sensors hold the forward run's outputs.  Synchronises.
- * Errors: ARG, STATE (already stepped), UNSUPPORTED (a force or Dirichlet
- * source: only additive mass sources are differentiated), OOM, CUDA,
- * NONFINITE. */
+ * Afterwards the simulation holds the forward end state and sensor outputs
+ * again.  Synchronises.  Errors: ARG (buffer too small), STATE (no pending
+ * forward run), OOM, CUDA, NONFINITE. */
+int kwgb_adjoint_backward(kwgb_sim* sim, double* grad_out, int64_t grad_len, void* cuda_stream);
+
+/* Both calls in one: kwgb_adjoint_forward (checkpoint_every > 0) then
+ * kwgb_adjoint_backward.  Errors as theirs. */
 int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
                  int64_t n_steps, int64_t checkpoint_every, double* J_out, double* grad_out,
                  int64_t grad_len, void* cuda_stream);

@@ -3,12 +3,14 @@
 SimulateFocal(phases, amps) runs the GPU time step with one additive mass
 source per transducer element driven by s_e(t) = A_e sin(omega t + phi_e)
 (sampled at t = (n + 1/2) dt) and returns J = mean |p| over a focal region
-and all steps.  Its backward pass uses the library's hand-written adjoint
-(kwgb_adjoint: checkpoints every K steps, segment recomputation, reverse
-steps) and the chain rule
+and all steps.  forward() makes one forward run (kwgb_adjoint_forward: J is
+accumulated from the focal points on the device; when an input needs a
+gradient the run also keeps a checkpoint every K steps, and the simulation
+that holds them is kept for backward()).  backward() runs the library's
+hand-written reverse pass (kwgb_adjoint_backward: segment recomputation,
+reverse steps) and the chain rule
     dJ/dA_e   = sum_n dJ/ds_e^n sin(omega t_n + phi_e),
     dJ/dphi_e = sum_n dJ/ds_e^n A_e cos(omega t_n + phi_e).
-When no input needs a gradient only the forward run is made.
 """
 
 import numpy as np
@@ -45,26 +47,36 @@ class FocalProblem:
         return sim
 
     def objective(self, phases, amps):
-        """J only (plain forward run through the sensor outputs)."""
+        """J only: one forward run, no checkpoints."""
         sim = self.simulation(phases, amps)
-        sid = sim.add_sensor(self.focal, kwgb.P_MAX)
-        total = np.zeros(len(self.focal))
-        # J = mean |p|: step one at a time and accumulate |p| at the focus
-        for _ in range(self.n_steps):
-            sim.step(1)
-            total += np.abs(sim.read_field("p").reshape(-1)[self.focal])
-        sim.close()
-        del sid
-        return total.sum() / (len(self.focal) * self.n_steps)
+        try:
+            return sim.adjoint_forward(self.focal, self.n_steps, checkpoint_every=0)
+        finally:
+            sim.close()
 
-    def value_and_grad(self, phases, amps):
+    def forward(self, phases, amps):
+        """Forward run that keeps its checkpoints: returns (J, simulation);
+        pass the simulation to backward()."""
         sim = self.simulation(phases, amps)
-        J, g = sim.adjoint(self.focal, self.n_steps, self.checkpoint_every)
-        self.last_device_bytes = sim.device_bytes
-        sim.close()
+        J = sim.adjoint_forward(self.focal, self.n_steps, self.checkpoint_every)
+        return J, sim
+
+    def backward(self, sim, phases, amps):
+        """Reverse pass of forward()'s run (closes the simulation): returns
+        dJ/dphases, dJ/damps and dJ/dsignal per element."""
+        try:
+            g = sim.adjoint_backward()
+            self.last_device_bytes = sim.device_bytes
+        finally:
+            sim.close()
         w = 2.0 * np.pi * self.freq
         dphi = np.array([(gr[0] * a * np.cos(w * self.t + ph)).sum() for gr, a, ph in zip(g, amps, phases)])
         damp = np.array([(gr[0] * np.sin(w * self.t + ph)).sum() for gr, a, ph in zip(g, amps, phases)])
+        return dphi, damp, g
+
+    def value_and_grad(self, phases, amps):
+        J, sim = self.forward(phases, amps)
+        dphi, damp, g = self.backward(sim, phases, amps)
         return J, dphi, damp, g
 
 
@@ -75,15 +87,18 @@ class SimulateFocal(torch.autograd.Function):
     def forward(ctx, phases, amps, problem):
         ph = phases.detach().double().cpu().numpy()
         am = amps.detach().double().cpu().numpy()
+        ctx.sim = None
         if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
-            J, dphi, damp, _ = problem.value_and_grad(ph, am)
-            ctx.save_for_backward(torch.from_numpy(dphi).to(phases.device, phases.dtype),
-                                  torch.from_numpy(damp).to(amps.device, amps.dtype))
+            J, ctx.sim = problem.forward(ph, am)
+            ctx.problem, ctx.ph, ctx.am = problem, ph, am
         else:
             J = problem.objective(ph, am)
         return torch.tensor(J, dtype=phases.dtype, device=phases.device)
 
     @staticmethod
     def backward(ctx, gJ):
-        dphi, damp = ctx.saved_tensors
+        dphi, damp, _ = ctx.problem.backward(ctx.sim, ctx.ph, ctx.am)
+        ctx.sim = None
+        dphi = torch.from_numpy(dphi).to(gJ.device, gJ.dtype)
+        damp = torch.from_numpy(damp).to(gJ.device, gJ.dtype)
         return gJ * dphi, gJ * damp, None

@@ -107,6 +107,19 @@ struct kwgb_sim {
     cudaStream_t last_stream = nullptr;
     int64_t launches = 0;       // kernels launched so far
     bool adjoint_done = false;
+    // adjoint: kwgb_adjoint_forward keeps what kwgb_adjoint_backward needs
+    float* adj_dout[3] = {nullptr, nullptr, nullptr};   // x_dens writes d_xi here when set (recomputation)
+    struct AdjRun {
+        bool pending = false;            // forward with checkpoints done, reverse pass not yet run
+        int64_t n_steps = 0, K = 0, n_obj = 0;
+        double w = 0.0;                  // 1 / (n_obj n_steps)
+        char* ck = nullptr;              // checkpoints (u, rho_xi, P) every K steps
+        char* fin = nullptr;             // forward end state
+        float* pobj = nullptr;           // p at the objective points, every step
+        int64_t* d_obj = nullptr;        // objective points
+        char* snap = nullptr;            // sensor accumulators after the forward run
+        std::vector<std::pair<void*, size_t>> sarr;
+    } adj;
     // one captured step, replayed by kwgb_step (CUDA graph)
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap = nullptr;         // stream the step is captured on
@@ -426,7 +439,6 @@ static cudaError_t zop(kwgb_sim* sim, int kind, float2* const* in, float2* const
 
 // spectrum -> gradient spectra (x still transformed): y fwd, z op, y inv
 static int grad_chain(kwgb_sim* sim, float2* in, float2* const out[3], int kind, cudaStream_t s) {
-    const GridC& g = sim->g;
     float2* i1[1] = {in};
     LK(ypass(sim, -1, i1, i1, 1, s));
     float2* zin[3] = {in, nullptr, nullptr};
@@ -463,7 +475,7 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
     LKM(ypass(sim, +1, sp, sp, 3, s), K_Y_INV_DIV);
     // Eq. 4d + source; lossless: Eq. 6 + sensors + R2C of p here
     XDensArgs da{};
-    for (int a = 0; a < 3; ++a) { da.D[a] = sp[a]; da.rho[a] = sim->rho[a]; }
+    for (int a = 0; a < 3; ++a) { da.D[a] = sp[a]; da.rho[a] = sim->rho[a]; da.dout[a] = sim->adj_dout[a]; }
     const SensorC sens = sensor_c(sim);
     if (sim->md.absorbing) {
         da.S = sim->P;
@@ -1145,50 +1157,51 @@ extern "C" int kwgb_apply_operator(kwgb_sim* sim, int op, const float* in, float
 
 
 // ------------------------------------------------------------------ adjoint
-// real field r -> spectra (T1, T2, T3) -> y fwd -> z operator -> y inv -> real field
-static int adj_chain(kwgb_sim* sim, float* const in[3], float* const out[3], int kind, cudaStream_t s) {
-    const GridC& g = sim->g;
-    float2* sp[3] = {sim->T1, sim->T2, sim->T3};
-    for (int a = 0; a < 3; ++a) LK(launch_x_r2c(g, in[a], g.nx, sp[a], s));
-    LK(ypass(sim, -1, sp, sp, 3, s));
-    LK(zop(sim, kind, sp, sp, s));
-    LK(ypass(sim, +1, sp, sp, 3, s));
-    for (int a = 0; a < 3; ++a) LK(launch_x_c2r(g, sp[a], out[a], g.nx, s));
-    return KWGB_OK;
-}
-
-// q1 <- IFT{k^{y-2} FT{q1}}, q2 <- IFT{k^{y-1} FT{q2}} (real fields, in place)
-static int adj_abs_chain(kwgb_sim* sim, float* q1, float* q2, cudaStream_t s) {
-    const GridC& g = sim->g;
-    float2* sp[3] = {sim->T1, sim->T2, nullptr};
-    LK(launch_x_r2c(g, q1, g.nx, sim->T1, s));
-    LK(launch_x_r2c(g, q2, g.nx, sim->T2, s));
-    LK(ypass(sim, -1, sp, sp, 2, s));
-    LK(zop(sim, Z_ABS, sp, sp, s));
-    LK(ypass(sim, +1, sp, sp, 2, s));
-    LK(launch_x_c2r(g, sim->T1, q1, g.nx, s));
-    LK(launch_x_c2r(g, sim->T2, q2, g.nx, s));
-    return KWGB_OK;
-}
-
 static int copy_dev(kwgb_sim* sim, void* dst, const void* src, size_t bytes, cudaStream_t s) {
     CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
     return KWGB_OK;
 }
 
-extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
-                            int64_t n_steps, int64_t checkpoint_every, double* J_out, double* grad_out,
-                            int64_t grad_len, void* cuda_stream) {
-    NvtxRange nvtx_("kwgb_adjoint");
+static size_t ck_bytes(kwgb_sim* sim) {
+    return 6 * (size_t)sim->N * sizeof(float) + sim->spec_elems * sizeof(float2);
+}
+
+// state (u, rho_xi, P) <-> a checkpoint slot
+static int save_ck(kwgb_sim* sim, char* dst, cudaStream_t s) {
+    const size_t F = (size_t)sim->N * sizeof(float);
+    for (int a = 0; a < 3; ++a) {
+        if (int e = copy_dev(sim, dst + a * F, sim->u[a], F, s)) return e;
+        if (int e = copy_dev(sim, dst + (3 + a) * F, sim->rho[a], F, s)) return e;
+    }
+    return copy_dev(sim, dst + 6 * F, sim->P, sim->spec_elems * sizeof(float2), s);
+}
+
+static int load_ck(kwgb_sim* sim, const char* src, int64_t step, cudaStream_t s) {
+    const size_t F = (size_t)sim->N * sizeof(float);
+    for (int a = 0; a < 3; ++a) {
+        if (int e = copy_dev(sim, sim->u[a], src + a * F, F, s)) return e;
+        if (int e = copy_dev(sim, sim->rho[a], src + (3 + a) * F, F, s)) return e;
+    }
+    if (int e = copy_dev(sim, sim->P, src + 6 * F, sim->spec_elems * sizeof(float2), s)) return e;
+    CK(cudaMemcpyAsync(sim->d_step, &step, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));              // the host value of step goes out of scope
+    return KWGB_OK;
+}
+
+extern "C" int kwgb_adjoint_forward(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
+                                    int64_t n_steps, int64_t checkpoint_every, double* J_out,
+                                    void* cuda_stream) {
+    NvtxRange nvtx_("kwgb_adjoint_forward");
     if (!sim) return KWGB_ERR_ARG;
     if (!sim->medium_set) return fail(sim, KWGB_ERR_STATE, "set the medium first");
     if (sim->steps != 0 || sim->frozen || sim->adjoint_done)
-        return fail(sim, KWGB_ERR_STATE, "kwgb_adjoint needs a simulation that has not stepped");
+        return fail(sim, KWGB_ERR_STATE, "the adjoint needs a simulation that has not stepped");
     if (objective != KWGB_OBJ_MEAN_ABS_P) return fail(sim, KWGB_ERR_ARG, "unknown objective");
-    for (auto& h : sim->hsrc)
-        if (h.mode != KWGB_ADDITIVE_MASS)
-            return fail(sim, KWGB_ERR_UNSUPPORTED, "the adjoint differentiates additive mass sources only");
-    if (!obj_idx || n_obj <= 0 || n_steps <= 0 || checkpoint_every <= 0 || !J_out)
+    if (checkpoint_every > 0)
+        for (auto& h : sim->hsrc)
+            if (h.mode != KWGB_ADDITIVE_MASS)
+                return fail(sim, KWGB_ERR_UNSUPPORTED, "the adjoint differentiates additive mass sources only");
+    if (!obj_idx || n_obj <= 0 || n_steps <= 0 || checkpoint_every < 0 || !J_out)
         return fail(sim, KWGB_ERR_ARG, "bad objective, step count or checkpoint interval");
     {
         std::vector<int64_t> u(obj_idx, obj_idx + n_obj);
@@ -1197,6 +1210,86 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
             if (u[i] < 0 || u[i] >= sim->N || (i && u[i] == u[i - 1]))
                 return fail(sim, KWGB_ERR_ARG, "objective indices must be unique and inside the grid");
     }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sim->last_stream = s;
+    auto& A = sim->adj;
+    const int64_t K = checkpoint_every;
+    // objective points become an internal sensor (p of every step is read from its slots)
+    int32_t osid = -1;
+    if (int e = kwgb_add_sensor(sim, obj_idx, n_obj, KWGB_P_MAX, &osid)) return e;
+    if (int e = freeze(sim)) return e;
+    sim->adjoint_done = true;
+    const int64_t slot0 = sim->hsens[osid].slot0;
+    A.pobj = static_cast<float*>(dalloc(sim, (size_t)n_steps * n_obj * sizeof(float)));
+    if (!A.pobj) return fail(sim, KWGB_ERR_OOM, "adjoint objective samples");
+    if (K > 0) {
+        const int64_t nck = (n_steps + K - 1) / K;
+        A.ck = static_cast<char*>(dalloc(sim, (size_t)nck * ck_bytes(sim)));
+        A.fin = static_cast<char*>(dalloc(sim, ck_bytes(sim)));
+        if (!A.ck || !A.fin) return fail(sim, KWGB_ERR_OOM, "adjoint checkpoints");
+        std::vector<int64_t> ov(obj_idx, obj_idx + n_obj);
+        if (int e = upload(sim, &A.d_obj, ov)) return e;
+    }
+    // ---- forward run, a checkpoint every K steps
+    for (int64_t n = 0; n < n_steps; ++n) {
+        if (K > 0 && n % K == 0)
+            if (int e = save_ck(sim, A.ck + (size_t)(n / K) * ck_bytes(sim), s)) return e;
+        if (int e = run_step(sim, s)) return e;
+        sim->steps++;
+        if (int e = copy_dev(sim, A.pobj + n * n_obj, sim->sens.p_sens + slot0, n_obj * sizeof(float), s)) return e;
+    }
+    if (K > 0) {
+        if (int e = save_ck(sim, A.fin, s)) return e;
+        // sensor accumulators as the forward run left them (the recomputation steps again)
+        const SensorC& sc_ = sim->sens;
+        const size_t N = (size_t)sim->N;
+        auto& sarr = A.sarr;
+        sarr.clear();
+        if (sim->n_slots) {
+            sarr.push_back({sc_.p_max, sim->n_slots * sizeof(float)});
+            sarr.push_back({sc_.p2, sim->n_slots * sizeof(double)});
+            sarr.push_back({sc_.p_sens, sim->n_slots * sizeof(float)});
+            if (sc_.p_min) sarr.push_back({sc_.p_min, sim->n_slots * sizeof(float)});
+        }
+        for (int k = 0; k < sc_.nfull; ++k) {
+            sarr.push_back({sc_.full_max[k], N * sizeof(float)});
+            sarr.push_back({sc_.full_p2[k], N * sizeof(double)});
+            if (sc_.full_min[k]) sarr.push_back({sc_.full_min[k], N * sizeof(float)});
+        }
+        if (sim->n_i) sarr.push_back({sim->I, 3 * sim->n_i * sizeof(double)});
+        if (sim->series_elems) sarr.push_back({sc_.series, sim->series_elems * sizeof(float)});
+        if (sim->useries_elems) sarr.push_back({sim->useries, sim->useries_elems * sizeof(float)});
+        size_t sbytes = 0;
+        for (auto& q : sarr) sbytes += q.second;
+        A.snap = static_cast<char*>(dalloc(sim, std::max<size_t>(sbytes, 16)));
+        if (!A.snap) return fail(sim, KWGB_ERR_OOM, "sensor snapshot");
+        size_t off = 0;
+        for (auto& q : sarr) {
+            if (int e = copy_dev(sim, A.snap + off, q.first, q.second, s)) return e;
+            off += q.second;
+        }
+    }
+    // ---- objective value (float64 on the host)
+    std::vector<float> hp((size_t)n_steps * n_obj);
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(hp.data(), A.pobj, hp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    A.w = 1.0 / ((double)n_obj * (double)n_steps);
+    double J = 0.0;
+    for (float v : hp) J += std::fabs((double)v);
+    *J_out = J * A.w;
+    A.n_steps = n_steps;
+    A.K = K;
+    A.n_obj = n_obj;
+    A.pending = K > 0;
+    return sync_and_flag(sim);
+}
+
+extern "C" int kwgb_adjoint_backward(kwgb_sim* sim, double* grad_out, int64_t grad_len, void* cuda_stream) {
+    NvtxRange nvtx_("kwgb_adjoint_backward");
+    if (!sim) return KWGB_ERR_ARG;
+    auto& A = sim->adj;
+    if (!A.pending)
+        return fail(sim, KWGB_ERR_STATE, "kwgb_adjoint_backward needs kwgb_adjoint_forward with checkpoints first");
     int64_t rows = 0, need = 0, max_nt = 1;
     for (auto& h : sim->hsrc) {
         rows += h.nsig;
@@ -1206,29 +1299,16 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
     if (grad_len < need || (need > 0 && !grad_out)) return fail(sim, KWGB_ERR_ARG, "gradient buffer too small");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     sim->last_stream = s;
-
-    // objective points become an internal sensor (p of every step is read from its slots)
-    int32_t osid = -1;
-    if (int e = kwgb_add_sensor(sim, obj_idx, n_obj, KWGB_P_MAX, &osid)) return e;
-    if (int e = freeze(sim)) return e;
-    const int64_t slot0 = sim->hsens[osid].slot0;
     const size_t N = (size_t)sim->N;
     const size_t F = N * sizeof(float);
-    const size_t SB = sim->spec_elems * sizeof(float2);
-    const int64_t K = checkpoint_every;
+    const int64_t n_steps = A.n_steps, K = A.K, n_obj = A.n_obj;
     const int64_t nck = (n_steps + K - 1) / K;
     const int64_t segK = std::min(K, n_steps);
-
-    // device memory of the adjoint
-    char* ck = static_cast<char*>(dalloc(sim, (size_t)nck * (6 * F + SB)));
-    char* fin = static_cast<char*>(dalloc(sim, 6 * F + SB));
-    float* seg = static_cast<float*>(dalloc(sim, (size_t)(segK + 1) * 6 * F));
-    const bool absorbing = sim->md.absorbing != 0;
-    const int nlam = absorbing ? 13 : 11;
-    float* lam = static_cast<float*>(dalloc(sim, nlam * F));
-    float* pobj = static_cast<float*>(dalloc(sim, (size_t)n_steps * n_obj * sizeof(float)));
+    // segment buffers: rho_xi^n (segK + 1 states) and d_xi (segK steps); adjoint fields
+    float* seg = static_cast<float*>(dalloc(sim, (size_t)(2 * segK + 1) * 3 * F));
+    float* lam = static_cast<float*>(dalloc(sim, 8 * F));
     double* grad = static_cast<double*>(dalloc(sim, (size_t)std::max<int64_t>(rows, 1) * max_nt * sizeof(double)));
-    if (!ck || !fin || !seg || !lam || !pobj || !grad) return fail(sim, KWGB_ERR_OOM, "adjoint buffers");
+    if (!seg || !lam || !grad) return fail(sim, KWGB_ERR_OOM, "adjoint buffers");
     // per signal row: its points and the source scale dt 2 / (3 dx) (the kernel divides by c0)
     std::vector<int32_t> rptr(1, 0), rnt;
     std::vector<int64_t> rpts;
@@ -1245,11 +1325,6 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
             rptr.push_back((int32_t)rpts.size());
             rnt.push_back((int32_t)h.nt);
         }
-    int64_t* d_obj = nullptr;
-    {
-        std::vector<int64_t> ov(obj_idx, obj_idx + n_obj);
-        if (int e = upload(sim, &d_obj, ov)) return e;
-    }
     int32_t *d_rptr = nullptr, *d_rnt = nullptr;
     int64_t* d_rpts = nullptr;
     float* d_rscale = nullptr;
@@ -1259,125 +1334,71 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
         if (int e = upload(sim, &d_rpts, rpts)) return e;
         if (int e = upload(sim, &d_rscale, rscale)) return e;
     }
-    auto save_state = [&](char* dst) -> int {
-        for (int a = 0; a < 3; ++a) {
-            if (int e = copy_dev(sim, dst + a * F, sim->u[a], F, s)) return e;
-            if (int e = copy_dev(sim, dst + (3 + a) * F, sim->rho[a], F, s)) return e;
-        }
-        return copy_dev(sim, dst + 6 * F, sim->P, SB, s);
-    };
-    auto load_state = [&](const char* src, int64_t step) -> int {
-        for (int a = 0; a < 3; ++a) {
-            if (int e = copy_dev(sim, sim->u[a], src + a * F, F, s)) return e;
-            if (int e = copy_dev(sim, sim->rho[a], src + (3 + a) * F, F, s)) return e;
-        }
-        if (int e = copy_dev(sim, sim->P, src + 6 * F, SB, s)) return e;
-        CK(cudaMemcpy(sim->d_step, &step, sizeof(int64_t), cudaMemcpyHostToDevice));
-        return KWGB_OK;
-    };
-    // ---- forward with checkpoints
-    for (int64_t n = 0; n < n_steps; ++n) {
-        if (n % K == 0)
-            if (int e = save_state(ck + (size_t)(n / K) * (6 * F + SB))) return e;
-        if (int e = run_step(sim, s)) return e;
-        sim->steps++;
-        if (int e = copy_dev(sim, pobj + n * n_obj, sim->sens.p_sens + slot0, n_obj * sizeof(float), s)) return e;
-    }
-    if (int e = save_state(fin)) return e;
-    // sensor accumulators as the forward run left them (the recomputation below steps again)
-    std::vector<std::pair<void*, size_t>> sarr;
-    const SensorC& sc_ = sim->sens;
-    if (sim->n_slots) {
-        sarr.push_back({sc_.p_max, sim->n_slots * sizeof(float)});
-        sarr.push_back({sc_.p2, sim->n_slots * sizeof(double)});
-        sarr.push_back({sc_.p_sens, sim->n_slots * sizeof(float)});
-        if (sc_.p_min) sarr.push_back({sc_.p_min, sim->n_slots * sizeof(float)});
-    }
-    for (int k = 0; k < sc_.nfull; ++k) {
-        sarr.push_back({sc_.full_max[k], N * sizeof(float)});
-        sarr.push_back({sc_.full_p2[k], N * sizeof(double)});
-        if (sc_.full_min[k]) sarr.push_back({sc_.full_min[k], N * sizeof(float)});
-    }
-    if (sim->n_i) sarr.push_back({sim->I, 3 * sim->n_i * sizeof(double)});
-    if (sim->series_elems) sarr.push_back({sc_.series, sim->series_elems * sizeof(float)});
-    if (sim->useries_elems) sarr.push_back({sim->useries, sim->useries_elems * sizeof(float)});
-    size_t sbytes = 0;
-    for (auto& a : sarr) sbytes += a.second;
-    char* snap = static_cast<char*>(dalloc(sim, std::max<size_t>(sbytes, 16)));
-    if (!snap) return fail(sim, KWGB_ERR_OOM, "sensor snapshot");
-    {
-        size_t off = 0;
-        for (auto& a : sarr) {
-            if (int e = copy_dev(sim, snap + off, a.first, a.second, s)) return e;
-            off += a.second;
-        }
-    }
-    // ---- objective value (float64 on the host)
-    std::vector<float> hp((size_t)n_steps * n_obj);
-    CK(cudaStreamSynchronize(s));
-    CK(cudaMemcpy(hp.data(), pobj, hp.size() * sizeof(float), cudaMemcpyDeviceToHost));
-    const double w = 1.0 / ((double)n_obj * (double)n_steps);
-    double J = 0.0;
-    for (float v : hp) J += std::fabs((double)v);
-    *J_out = J * w;
-    // ---- reverse pass
-    CK(cudaMemsetAsync(lam, 0, nlam * F, s));
+    CK(cudaMemsetAsync(lam, 0, 8 * F, s));
     CK(cudaMemsetAsync(grad, 0, (size_t)std::max<int64_t>(rows, 1) * max_nt * sizeof(double), s));
-    AdjFields af{};
-    af.lam_p = lam;
-    for (int a = 0; a < 3; ++a) {
-        af.lam_u[a] = lam + (1 + a) * N;
-        af.lam_rho[a] = lam + (4 + a) * N;
-        af.w[a] = lam + (8 + a) * N;
-    }
-    af.lam_src = lam + 7 * N;
-    float* q1 = absorbing ? lam + 11 * N : nullptr;
-    float* q2 = absorbing ? lam + 12 * N : nullptr;
-    af.abs1 = q1;
-    af.abs2 = q2;
     const GridC& g = sim->g;
-    auto seg_rho = [&](int64_t k, int a) { return seg + ((size_t)k * 6 + a) * N; };
-    auto seg_u = [&](int64_t k, int a) { return seg + ((size_t)k * 6 + 3 + a) * N; };
+    const bool absorbing = sim->md.absorbing != 0;
+    auto seg_rho = [&](int64_t k, int a) { return seg + ((size_t)k * 3 + a) * N; };
+    auto seg_d = [&](int64_t k, int a) { return seg + ((size_t)(segK + 1 + k) * 3 + a) * N; };
+    AdjX ax{};
+    ax.lam_p = lam;
+    for (int a = 0; a < 3; ++a) {
+        ax.lam_u[a] = lam + (1 + a) * N;
+        ax.lam_rho[a] = lam + (4 + a) * N;
+    }
+    ax.lam_src = lam + 7 * N;
+    float2* sp[3] = {sim->T1, sim->T2, sim->T3};
+    for (int a = 0; a < 3; ++a) ax.sp[a] = sp[a];
+    float2* ab[3] = {sim->T1, sim->T2, nullptr};
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t n0 = c * K, n1 = std::min(n0 + K, n_steps);
-        if (int e = load_state(ck + (size_t)c * (6 * F + SB), n0)) return e;
+        // recompute the segment, keeping rho_xi^n and the d_xi of every step
+        if (int e = load_ck(sim, A.ck + (size_t)c * ck_bytes(sim), n0, s)) return e;
         for (int64_t n = n0; n < n1; ++n) {
-            for (int a = 0; a < 3; ++a)
+            for (int a = 0; a < 3; ++a) {
                 if (int e = copy_dev(sim, seg_rho(n - n0, a), sim->rho[a], F, s)) return e;
-            if (int e = run_step(sim, s)) return e;
-            for (int a = 0; a < 3; ++a)
-                if (int e = copy_dev(sim, seg_u(n - n0, a), sim->u[a], F, s)) return e;
+                sim->adj_dout[a] = seg_d(n - n0, a);
+            }
+            const int e = launch_step(sim, s);
+            for (int a = 0; a < 3; ++a) sim->adj_dout[a] = nullptr;
+            if (e) return e;
         }
         for (int a = 0; a < 3; ++a)
             if (int e = copy_dev(sim, seg_rho(n1 - n0, a), sim->rho[a], F, s)) return e;
+        // reverse steps of the segment
         for (int64_t n = n1 - 1; n >= n0; --n) {
             const int64_t k = n - n0;
-            LK(launch_adj_obj(n_obj, d_obj, pobj + n * n_obj, w, af.lam_p, s));
-            if (absorbing) {                                                      // Eq. 8 backwards
-                LK(launch_adj_absprep(g, sim->md, af.lam_p, q1, q2, s));
-                if (int e = adj_abs_chain(sim, q1, q2, s)) return e;
-            }
-            float* uin[3] = {seg_u(k, 0), seg_u(k, 1), seg_u(k, 2)};
-            if (int e = adj_chain(sim, uin, af.w, Z_DIV, s)) return e;               // d_xi (Eq. 4c)
             for (int a = 0; a < 3; ++a) {
-                af.rho_before[a] = seg_rho(k, a);
-                af.rho_after[a] = seg_rho(k + 1, a);
+                ax.rho_before[a] = seg_rho(k, a);
+                ax.rho_after[a] = seg_rho(k + 1, a);
+                ax.d[a] = seg_d(k, a);
             }
-            LK(launch_adj_dens(g, sim->md, af, s));
-            LK(launch_adj_src((int)rows, d_rptr, d_rpts, d_rscale, d_rnt, af.lam_src, sim->md, grad, max_nt, n, s));
-            if (int e = adj_chain(sim, af.w, af.w, Z_DIV_FWD, s)) return e;          // transpose of Eq. 4c
-            LK(launch_adj_vel(g, sim->md, af, s));
-            if (int e = adj_chain(sim, af.w, af.w, Z_DIV, s)) return e;              // transpose of Eq. 4a
-            LK(launch_adj_psum(g, af, s));
+            LK(launch_adj_obj(n_obj, A.d_obj, A.pobj + n * n_obj, A.w, ax.lam_p, s));
+            if (absorbing) {                                                      // Eq. 8 backwards
+                LK(launch_adj_x_absprep(g, sim->md, ax, s));
+                LK(ypass(sim, -1, ab, ab, 2, s));
+                LK(zop(sim, Z_ABS, ab, ab, s));
+                LK(ypass(sim, +1, ab, ab, 2, s));
+            }
+            LK(launch_adj_x_dens(g, sim->md, ax, s));                            // Eqs. 6, 4d backwards
+            LK(launch_adj_src((int)rows, d_rptr, d_rpts, d_rscale, d_rnt, ax.lam_src, sim->md, grad, max_nt, n, s));
+            LK(ypass(sim, -1, sp, sp, 3, s));                                     // transpose of Eq. 4c
+            LK(zop(sim, Z_DIV_FWD, sp, sp, s));
+            LK(ypass(sim, +1, sp, sp, 3, s));
+            LK(launch_adj_x_vel(g, sim->md, ax, s));                             // Eq. 4b backwards
+            LK(ypass(sim, -1, sp, sp, 3, s));                                     // transpose of Eq. 4a
+            LK(zop(sim, Z_DIV, sp, sp, s));
+            LK(ypass(sim, +1, sp, sp, 3, s));
+            LK(launch_adj_x_p(g, sim->md, ax, s));
         }
     }
     // ---- put back the forward end state and the sensors
-    if (int e = load_state(fin, n_steps)) return e;
+    if (int e = load_ck(sim, A.fin, n_steps, s)) return e;
     {
         size_t off = 0;
-        for (auto& a : sarr) {
-            if (int e = copy_dev(sim, a.first, snap + off, a.second, s)) return e;
-            off += a.second;
+        for (auto& q : A.sarr) {
+            if (int e = copy_dev(sim, q.first, A.snap + off, q.second, s)) return e;
+            off += q.second;
         }
     }
     std::vector<double> hg((size_t)std::max<int64_t>(rows, 1) * max_nt);
@@ -1387,8 +1408,22 @@ extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj
     for (auto& h : sim->hsrc)
         for (int64_t q = 0; q < h.nsig; ++q, ++r)
             for (int64_t n = 0; n < h.nt; ++n) grad_out[o++] = hg[(size_t)r * max_nt + n];
-    sim->adjoint_done = true;
+    A.pending = false;
     return sync_and_flag(sim);
+}
+
+extern "C" int kwgb_adjoint(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, int objective,
+                            int64_t n_steps, int64_t checkpoint_every, double* J_out, double* grad_out,
+                            int64_t grad_len, void* cuda_stream) {
+    NvtxRange nvtx_("kwgb_adjoint");
+    if (!sim) return KWGB_ERR_ARG;
+    if (checkpoint_every <= 0) return fail(sim, KWGB_ERR_ARG, "bad objective, step count or checkpoint interval");
+    int64_t need = 0;
+    for (auto& h : sim->hsrc) need += h.nsig * h.nt;
+    if (grad_len < need || (need > 0 && !grad_out)) return fail(sim, KWGB_ERR_ARG, "gradient buffer too small");
+    if (int e = kwgb_adjoint_forward(sim, obj_idx, n_obj, objective, n_steps, checkpoint_every, J_out, cuda_stream))
+        return e;
+    return kwgb_adjoint_backward(sim, grad_out, grad_len, cuda_stream);
 }
 
 extern "C" int kwgb_debug_wait_fault(kwgb_sim* sim, int on) {

@@ -20,9 +20,10 @@ struct XDensK {
 };
 
 
-// DIRICHLET: the launch has Dirichlet pressure sources (a separate
-// instantiation, so that the common path carries no code for them).
-template <int LOGM, bool FUSED_EOS, bool DIRICHLET>
+// DIRICHLET: the launch has Dirichlet pressure sources; DOUT: it also writes
+// the Eq. 4c derivatives d_xi (the adjoint's recomputation).  Separate
+// instantiations, so that the common path carries no code for them.
+template <int LOGM, bool FUSED_EOS, bool DIRICHLET, bool DOUT>
 __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(const XDensK K) {
     using Sh = XShape<LOGM>;
     using St = XStage<LOGM>;
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
                 }
                 const float2 rn = make_float2(nx_, ny_);
                 if (valid) st2(rho_xi + rb + x, rn);
+                if (DOUT && valid) st2(pick3f(K.a.dout, xi) + rb + x, d[m]);
                 rt[m] = cadd(rt[m], rn);
                 s[m] = make_float2(fmaf(r0[m].x, d[m].x, s[m].x), fmaf(r0[m].y, d[m].y, s[m].y));
             }
@@ -371,13 +373,17 @@ cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src, c
     XDensK K{g, m, src, dsrc, sens, st, a};
     const bool fused = !m.absorbing;
     const bool dir = dsrc.row_ptr != nullptr;
+    const bool dout = a.dout[0] != nullptr;
+    if (dout && dir) return cudaErrorInvalidValue;          // the adjoint takes no Dirichlet sources
     switch (g.lognx - 1) {
-#define CASE(L)                                                                                   \
-    case L:                                                                                       \
-        if (fused && dir) return launch_persistent<L>(x_dens_kernel<L, true, true>, g, K, s);   \
-        if (fused) return launch_persistent<L>(x_dens_kernel<L, true, false>, g, K, s);         \
-        if (dir) return launch_persistent<L>(x_dens_kernel<L, false, true>, g, K, s);           \
-        return launch_persistent<L>(x_dens_kernel<L, false, false>, g, K, s);
+#define CASE(L)                                                                                          \
+    case L:                                                                                              \
+        if (dout && fused) return launch_persistent<L>(x_dens_kernel<L, true, false, true>, g, K, s);   \
+        if (dout) return launch_persistent<L>(x_dens_kernel<L, false, false, true>, g, K, s);           \
+        if (fused && dir) return launch_persistent<L>(x_dens_kernel<L, true, true, false>, g, K, s);    \
+        if (fused) return launch_persistent<L>(x_dens_kernel<L, true, false, false>, g, K, s);          \
+        if (dir) return launch_persistent<L>(x_dens_kernel<L, false, true, false>, g, K, s);            \
+        return launch_persistent<L>(x_dens_kernel<L, false, false, false>, g, K, s);
         KWGB_LOGM_CASES(CASE)
 #undef CASE
     }

@@ -141,6 +141,7 @@ struct XDensArgs {
     float2* R;                // x-R2C of rho         (absorbing only)
     float* rho_tot;           // rho as real rows of pitch 2*nhp (absorbing only)
     float2* P;                // non-absorbing: x-R2C of p (EOS fused here)
+    float* dout[3];           // optional (adjoint recomputation): d_xi = Eq. 4c derivative, pitch nx
 };
 cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src, const SourceC& dsrc,
                           const SensorC& sens, const StepC& st, const XDensArgs& a,
@@ -177,27 +178,28 @@ cudaError_t launch_intensity_accum(int64_t n, const int64_t* idx, const GridC& g
                                    const int64_t* step, int skip_first, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t s);
 
-// ---- adjoint (reverse-mode) pointwise kernels --------------------------
-struct AdjFields {
-    float* lam_p;             // lambda of p^{n+1} (in), later of p^n
+// ---- adjoint (reverse-mode) step ---------------------------------------
+// Fields of one reverse step; the x passes read and write the spectra sp[]
+// in place (kernels_adj.cu).
+struct AdjX {
+    float* lam_p;             // lambda of p^{n+1} (adj_x_dens in), of p^n (adj_x_p out)
     float* lam_u[3];          // lambda of u^{n+1/2} -> of u^{n-1/2}
     float* lam_rho[3];        // lambda of rho_xi^{n+1} -> of rho_xi^n
     float* lam_src;           // sum_xi lambda of rho_xi^{n+1} (source gradient)
-    float* w[3];              // work: d_xi -> lambda_d_xi -> (Eq. 4a op) -> lambda_g_xi -> ...
-    const float* rho_before[3];
-    const float* rho_after[3];
-    const float* abs1;        // absorbing: IFT{k^{y-2} FT{c0^2 tau lambda_p}} (else null)
-    const float* abs2;        //            IFT{k^{y-1} FT{-c0^2 eta lambda_p}}
+    const float* rho_before[3];   // rho_xi^n
+    const float* rho_after[3];    // rho_xi^{n+1}
+    const float* d[3];        // d_xi of the step (Eq. 4c derivative, from the recomputation)
+    float2* sp[3];            // spectra (x transformed), pitch nhp
 };
-// Eq. 8 backwards, first half: q1 = c0^2 tau lambda_p, q2 = -c0^2 eta lambda_p
-cudaError_t launch_adj_absprep(const GridC& g, const Medium& m, const float* lam_p, float* q1, float* q2,
-                               cudaStream_t s);
-// Eq. 6 (and Eq. 8) and Eq. 4d backwards: lambda_rho_xi, lambda_d_xi (into w), lambda_src
-cudaError_t launch_adj_dens(const GridC& g, const Medium& m, const AdjFields& a, cudaStream_t s);
-// Eq. 4b backwards: w holds D_f lambda_d on entry and lambda_g on exit; lambda_u updated
-cudaError_t launch_adj_vel(const GridC& g, const Medium& m, const AdjFields& a, cudaStream_t s);
-// lambda_p = -(w0 + w1 + w2)
-cudaError_t launch_adj_psum(const GridC& g, const AdjFields& a, cudaStream_t s);
+// absorbing: R2C of c0^2 tau lambda_p -> sp[0] and of -c0^2 eta lambda_p -> sp[1]
+cudaError_t launch_adj_x_absprep(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
+// [absorbing: C2R of the k^{y-2} / k^{y-1} results in sp[0], sp[1]] -> Eq. 6 / 4d backwards
+// -> lambda_rho, lambda_src -> R2C of lambda_d_xi -> sp[xi]
+cudaError_t launch_adj_x_dens(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
+// C2R of sp[xi] (Eq. 4a op of lambda_d) -> Eq. 4b backwards -> lambda_u -> R2C of lambda_g_xi -> sp[xi]
+cudaError_t launch_adj_x_vel(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
+// lambda_p = -(C2R sp[0] + C2R sp[1] + C2R sp[2])
+cudaError_t launch_adj_x_p(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
 // lambda_p[idx_k] += weight * sign(p_k) for the objective points
 cudaError_t launch_adj_obj(int64_t n, const int64_t* idx, const float* p, double weight, float* lam_p,
                            cudaStream_t s);

@@ -6,14 +6,20 @@
 // code paths that must not allocate after initialisation, because cudaMalloc
 // can synchronise the device and can fail once memory has been committed
 // elsewhere.  This entry point therefore takes its scratch space from one
-// file-scope __device__ array instead of allocating.  The array is created
-// when the library is loaded and every GPU that loads the library holds it
-// until the process exits: about 4.7 MB, enough for grids up to 64 x 64 x 64.
+// file-scope __device__ array instead of allocating: about 4.7 MB, enough for
+// grids up to 64 x 64 x 64, which every GPU that loads the library's device
+// code holds until the process exits.  With CUDA's lazy module loading that
+// code (and the array) is loaded on the first call on each device, so that
+// first call should be made at start-up.
 //
 // The operation is the same chain kwgb_apply_operator runs for
 // KWGB_OP_GRAD_FWD / KWGB_OP_GRAD_BWD (x R2C, y FFT, z FFT + operator + z
 // inverse, y inverse, x C2R) through the same kernels; only the scratch
-// spectra and the small tables live in the static array.
+// spectra and the small tables live in the static array.  The twiddle table
+// is uploaded once per device at set-up; the per-grid wavenumber and shift
+// tables are computed on the device in float64 by a small kernel, so a call
+// after the first enqueues kernels and one memset and copies nothing from
+// the host.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -52,6 +58,7 @@ int report(char* buf, size_t len, int code, const char* msg) {
 std::mutex g_setup_mu;
 float2* g_base[kMaxDevices];     // device address of the scratch array, per device
 int g_sms[kMaxDevices];
+bool g_wait_fault = false;       // test hook: tile loads expect 16 bytes more than they receive
 
 }  // namespace
 
@@ -61,7 +68,8 @@ int g_sms[kMaxDevices];
 static __device__ __align__(256) float2 g_static_scratch[kTotal];
 
 // Once per device, with that device current: look up the scratch array's
-// device address and the SM count.
+// device address and the SM count, and upload the (grid-independent) twiddle
+// table.  Synchronises the device once.
 static int static_setup(int dev, float2** base, int* sms, char* err, size_t errlen) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
     if (g_base[dev] == nullptr) {
@@ -74,6 +82,15 @@ static int static_setup(int dev, float2** base, int* sms, char* err, size_t errl
         int n = 0;
         e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return report(err, errlen, KWGB_ERR_CUDA, "cudaDeviceGetAttribute failed");
+        static float2 tw[TW_TOTAL];               // the same on every device
+        static bool filled = false;
+        if (!filled) fill_twiddle_table(tw);
+        filled = true;
+        e = cudaMemcpy(p + kOffTw, tw, sizeof(tw), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return report(err, errlen, KWGB_ERR_CUDA, "uploading the twiddle table into the static scratch failed");
+        }
         g_sms[dev] = n;
         g_base[dev] = p;
     }
@@ -82,9 +99,29 @@ static int static_setup(int dev, float2** base, int* sms, char* err, size_t errl
     return KWGB_OK;
 }
 
-static double wavenumber_static(int j, int n, double d) {
-    const int m = j < n / 2 ? j : j - n;                  // Eq. 5, even n
-    return (double)m * 2.0 * kPi / (d * (double)n);
+// Per-grid tables, computed in float64 on the device: for each axis a the
+// wavenumbers k_j (FFT storage order, the Nyquist bin at -n/2) and the shift
+// operator i k exp(+i k d / 2) of the staggered gradient, stored as float.
+// One block; thread j serves entry j of every axis.
+struct StaticTableArgs {
+    int len[3];       // entries per axis: nx/2 + 1, ny, nz
+    int n[3];
+    double d[3];
+    float* k[3];
+    float2* df[3];
+};
+
+__global__ void static_tables_kernel(StaticTableArgs a) {
+    const int j = threadIdx.x;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (j >= a.len[ax]) continue;
+        const int m = j < a.n[ax] / 2 ? j : j - a.n[ax];
+        const double k = (double)m * 2.0 * kPi / (a.d[ax] * (double)a.n[ax]);
+        double sn, cs;
+        sincos(k * a.d[ax] / 2.0, &sn, &cs);
+        a.k[ax][j] = (float)k;
+        a.df[ax][j] = make_float2((float)(-k * sn), (float)(k * cs));
+    }
 }
 
 static int ilog2_static(int v) {
@@ -109,7 +146,8 @@ extern "C" int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const fl
     const double dd[3] = {desc->dx, desc->dy, desc->dz};
     for (int a = 0; a < 3; ++a)
         if (!(dd[a] > 0) || !std::isfinite(dd[a])) return report(err, errlen, KWGB_ERR_ARG, "spacing must be positive");
-    if (!(desc->dt > 0) || !(desc->c_ref > 0)) return report(err, errlen, KWGB_ERR_ARG, "dt and c_ref must be positive");
+    if (!(desc->dt > 0) || !(desc->c_ref > 0) || !std::isfinite(desc->dt) || !std::isfinite(desc->c_ref))
+        return report(err, errlen, KWGB_ERR_ARG, "dt and c_ref must be positive and finite");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -131,32 +169,28 @@ extern "C" int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const fl
     g.hk2 = (float)((desc->c_ref * desc->dt / 2.0) * (desc->c_ref * desc->dt / 2.0));
     g.num_sms = sms;
 
-    // tables, built here in float64 and copied into the scratch (fixed-size host arrays)
-    static float2 tw[TW_TOTAL];                 // constant; filled once under the setup lock
     {
         std::lock_guard<std::mutex> lk(g_setup_mu);
-        static bool filled = false;
-        if (!filled) fill_twiddle_table(tw);
-        filled = true;
+        g.wait_fault_tx = g_wait_fault ? 16u : 0u;
     }
-    float kt[256];
-    float2 df[256];
-    const int klen[3] = {g.nh, g.ny, g.nz};
+
+    // per-grid tables on the device, the status word cleared
+    float* kbase = reinterpret_cast<float*>(base + kOffK);
     const int koff[3] = {0, kMaxN / 2 + 1, kMaxN / 2 + 1 + kMaxN};
     const int doff[3] = {0, 64, 128};
-    for (int a = 0; a < 3; ++a)
-        for (int j = 0; j < klen[a]; ++j) {
-            const double k = wavenumber_static(j, (int)n[a], dd[a]);
-            kt[koff[a] + j] = (float)k;
-            df[doff[a] + j] = make_float2((float)(-k * std::sin(k * dd[a] / 2.0)), (float)(k * std::cos(k * dd[a] / 2.0)));
-        }
-    float* kbase = reinterpret_cast<float*>(base + kOffK);
-    if (cudaMemcpyAsync(base + kOffTw, tw, sizeof(tw), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(kbase, kt, sizeof(kt), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(base + kOffDf, df, sizeof(df), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(base + kOffFlag, 0, sizeof(int), s) != cudaSuccess) {
+    StaticTableArgs ta;
+    const int klen[3] = {g.nh, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a) {
+        ta.len[a] = klen[a];
+        ta.n[a] = (int)n[a];
+        ta.d[a] = dd[a];
+        ta.k[a] = kbase + koff[a];
+        ta.df[a] = base + kOffDf + doff[a];
+    }
+    static_tables_kernel<<<1, kMaxN, 0, s>>>(ta);
+    if (cudaGetLastError() != cudaSuccess || cudaMemsetAsync(base + kOffFlag, 0, sizeof(int), s) != cudaSuccess) {
         cudaGetLastError();
-        return report(err, errlen, KWGB_ERR_CUDA, "copying the tables into the static scratch failed");
+        return report(err, errlen, KWGB_ERR_CUDA, "preparing the tables in the static scratch failed");
     }
     g.t.tw = base + kOffTw;
     g.t.kx = kbase + koff[0];
@@ -182,5 +216,32 @@ extern "C" int kwgb_gradient_static(const kwgb_grid_desc* desc, int op, const fl
     if (e == cudaSuccess) e = launch_y_pass(g, +1, all, sp, 3, flag, s);
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = launch_x_c2r(g, sp[a], outs[a], g.nx, s);
     if (e != cudaSuccess) return report(err, errlen, KWGB_ERR_CUDA, cudaGetErrorString(e));
+    return KWGB_OK;
+}
+
+extern "C" int kwgb_gradient_static_status(void* cuda_stream, char* err, size_t errlen) {
+    report(err, errlen, KWGB_OK, "");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return report(err, errlen, KWGB_ERR_CUDA, "no usable current device");
+    float2* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mu);
+        base = g_base[dev];
+    }
+    if (base == nullptr)
+        return report(err, errlen, KWGB_ERR_STATE, "no kwgb_gradient_static call on this device yet");
+    int flag = 0;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, base + kOffFlag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return report(err, errlen, KWGB_ERR_CUDA, cudaGetErrorString(e));
+    if (flag & 2) return report(err, errlen, KWGB_ERR_TIMEOUT, "a bounded device wait ran out (TMA tile load)");
+    if (flag & 1) return report(err, errlen, KWGB_ERR_NONFINITE, "non-finite value");
+    return KWGB_OK;
+}
+
+extern "C" int kwgb_gradient_static_debug_wait_fault(int on) {
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    g_wait_fault = on != 0;
     return KWGB_OK;
 }

@@ -315,6 +315,9 @@ __device__ __forceinline__ const float2* pick3(const float2* const (&p)[3], int 
 __device__ __forceinline__ float* pick3f(float* const (&p)[3], int i) {
     return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);
 }
+__device__ __forceinline__ const float* pick3c(const float* const (&p)[3], int i) {
+    return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);
+}
 __device__ __forceinline__ float2* pick3w(float2* const (&p)[3], int i) {
     return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);
 }

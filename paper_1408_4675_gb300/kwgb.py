@@ -87,6 +87,10 @@ def load():
     L.kwgb_kernel_name.restype = ctypes.c_char_p
     L.kwgb_adjoint.argtypes = [vp, vp, i64, ctypes.c_int, i64, i64, ctypes.POINTER(ctypes.c_double), vp, i64, vp]
     L.kwgb_adjoint.restype = ctypes.c_int
+    L.kwgb_adjoint_forward.argtypes = [vp, vp, i64, ctypes.c_int, i64, i64, ctypes.POINTER(ctypes.c_double), vp]
+    L.kwgb_adjoint_forward.restype = ctypes.c_int
+    L.kwgb_adjoint_backward.argtypes = [vp, vp, i64, vp]
+    L.kwgb_adjoint_backward.restype = ctypes.c_int
     L.kwgb_set_series_capacity.argtypes = [vp, i32, i64]
     L.kwgb_set_series_capacity.restype = ctypes.c_int
     L.kwgb_state_bytes.argtypes = [vp]
@@ -97,6 +101,13 @@ def load():
     L.kwgb_load_state.restype = ctypes.c_int
     L.kwgb_debug_wait_fault.argtypes = [vp, ctypes.c_int]
     L.kwgb_debug_wait_fault.restype = ctypes.c_int
+    L.kwgb_gradient_static.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int, vp, vp, vp, vp, vp,
+                                       ctypes.c_char_p, ctypes.c_size_t]
+    L.kwgb_gradient_static.restype = ctypes.c_int
+    L.kwgb_gradient_static_status.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    L.kwgb_gradient_static_status.restype = ctypes.c_int
+    L.kwgb_gradient_static_debug_wait_fault.argtypes = [ctypes.c_int]
+    L.kwgb_gradient_static_debug_wait_fault.restype = ctypes.c_int
     L.kwgb_destroy.argtypes = [vp]
     L.kwgb_destroy.restype = None
     for name in ("kwgb_create", "kwgb_set_allocator", "kwgb_set_medium", "kwgb_set_initial_pressure",
@@ -319,6 +330,29 @@ class Simulation:
             out.append(g[o:o + a * b].reshape(a, b))
             o += a * b
         return J.value, out
+
+    def adjoint_forward(self, obj_idx, n_steps, checkpoint_every=50, stream=None):
+        """Run n_steps forward and return J = mean |p| over obj_idx; with
+        checkpoint_every > 0 the simulation keeps the checkpoints that
+        adjoint_backward() needs, with 0 it computes J only."""
+        obj = np.ascontiguousarray(np.asarray(obj_idx, dtype=np.int64))
+        J = ctypes.c_double()
+        self._check(self.L.kwgb_adjoint_forward(self.h, _ptr(obj), obj.size, 0, int(n_steps), int(checkpoint_every),
+                                                ctypes.byref(J), _stream_ptr(stream)))
+        return J.value
+
+    def adjoint_backward(self, stream=None):
+        """Reverse pass of the preceding adjoint_forward(); returns
+        [dJ/dsignal per source, shaped (n_signals, n_t)]."""
+        shapes = [tuple(s) for s in self._src_shapes]
+        total = sum(a * b for a, b in shapes)
+        g = np.zeros(max(total, 1), dtype=np.float64)
+        self._check(self.L.kwgb_adjoint_backward(self.h, _ptr(g), g.size, _stream_ptr(stream)))
+        out, o = [], 0
+        for a, b in shapes:
+            out.append(g[o:o + a * b].reshape(a, b))
+            o += a * b
+        return out
 
     def status(self):
         return self.L.kwgb_status(self.h)

@@ -119,6 +119,25 @@ def test_series_capacity_validation_without_device():
     sim.close()
 
 
+def test_static_gradient_validates_without_device(lib):
+    """kwgb_gradient_static checks its arguments before any CUDA call: null
+    pointers and non-finite steps are ARG, grids beyond its fixed scratch
+    UNSUPPORTED, each with a message in the caller's buffer."""
+    err = ctypes.create_string_buffer(128)
+    x = ctypes.c_void_p(16)               # never dereferenced: validation fails first
+    d = _desc(n=(16, 16, 16))
+    assert lib.kwgb_gradient_static(ctypes.byref(d), kwgb.OP_GRAD_FWD, None, x, x, x, None, err, 128) == -1
+    assert lib.kwgb_gradient_static(ctypes.byref(d), 7, x, x, x, x, None, err, 128) == -1
+    d = _desc(n=(128, 16, 16))
+    assert lib.kwgb_gradient_static(ctypes.byref(d), kwgb.OP_GRAD_FWD, x, x, x, x, None, err, 128) == -7
+    assert b"[8, 64]" in err.value
+    for field in ("dt", "c_ref"):
+        d = _desc(n=(16, 16, 16))
+        setattr(d, field, float("nan"))
+        assert lib.kwgb_gradient_static(ctypes.byref(d), kwgb.OP_GRAD_BWD, x, x, x, x, None, err, 128) == -1
+        assert b"finite" in err.value
+
+
 def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     """No CPU fallback: without libkwgb.so the binding raises instead of computing."""
     monkeypatch.setattr(kwgb, "LIB_PATH", str(tmp_path / "libkwgb.so"))

@@ -1,6 +1,7 @@
 """GPU adjoint (kwgb_adjoint) against the FP64 oracle adjoint (lossless and
 absorbing media), checkpoint
-invariance, and the autograd wrapper against central finite differences.
+invariance, the autograd wrapper against central finite differences, and its
+forward-only and deferred-backward semantics.
 
 Tolerances: objective J 1e-3 relative; per-sample gradients dJ/ds relative
 L2 2e-3 against the oracle adjoint; phase gradients 1e-2 against FP32
@@ -104,3 +105,36 @@ def test_autograd_function_matches_finite_differences(kw):
         d[e] = h
         fd = (prob.objective(cfg["phases"] + d, cfg["amps"]) - prob.objective(cfg["phases"] - d, cfg["amps"])) / (2 * h)
         assert abs(fd - ph.grad[e].item()) <= 1e-2 * max(abs(fd), 1e-3 * abs(J.item())), (e, fd, ph.grad[e].item())
+
+
+def test_forward_only_and_deferred_backward(kw):
+    """SimulateFocal without a gradient makes one forward run (J from the
+    device-side objective samples, no checkpoints) and equals J taken by
+    stepping and reading p; with a gradient, forward() keeps the run's
+    checkpoints and backward() runs its reverse pass, which matches
+    value_and_grad bitwise."""
+    import torch
+    from paper_1408_4675_gb300.autograd import FocalProblem, SimulateFocal
+    steps = 40
+    cfg = _problem(n=32, steps=steps)
+    prob = FocalProblem(cfg, n_steps=steps, checkpoint_every=10)
+    sim = prob.simulation(cfg["phases"], cfg["amps"])
+    total = 0.0
+    for _ in range(steps):
+        sim.step(1)
+        total += np.abs(sim.read_field("p").reshape(-1)[prob.focal].astype(np.float64)).sum()
+    sim.close()
+    J_hand = total / (len(prob.focal) * steps)
+    ph = torch.tensor(cfg["phases"], dtype=torch.float64)
+    am = torch.tensor(cfg["amps"], dtype=torch.float64)
+    J0 = SimulateFocal.apply(ph, am, prob)
+    assert abs(J0.item() - J_hand) <= 1e-5 * J_hand, (J0.item(), J_hand)   # p read back through a C2R
+    ph.requires_grad_()
+    am.requires_grad_()
+    J1 = SimulateFocal.apply(ph, am, prob)
+    assert J1.item() == J0.item()
+    J1.backward()
+    J2, dphi, damp, _ = prob.value_and_grad(cfg["phases"], cfg["amps"])
+    assert J2 == J1.item()
+    np.testing.assert_array_equal(ph.grad.numpy(), dphi)
+    np.testing.assert_array_equal(am.grad.numpy(), damp)
