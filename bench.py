@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=3, choices=[3, 4])
-    ap.add_argument("--n", type=int, default=None,
+    ap.add_argument("--grid", "--n", dest="n", type=int, default=None,
                     help="cubic grid size override (same recipe; for profiling small cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
@@ -229,24 +229,22 @@ def ncu_traffic(kernel, shape):
 
 
 # ---------------------------------------------------------------- oracle (CPU)
-def oracle_sample(cfg_id, n_sample, steps):
-    """Time the FP64 oracle on the same recipe at n_sample^3; returns seconds
-    per step and the threads used."""
+def oracle_timed(cfg_id, n, warmup, steps):
+    """Time the FP64 oracle on the workload itself (same grid, medium, sources
+    and sensors): build it (not timed), run `warmup` steps, then time `steps`
+    steps one by one.  Returns (seconds per step, per-step list, threads)."""
     from oracle import kspace
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from helpers import oracle_from_config
-    cfg = inputs.make_config(cfg_id, n=n_sample, n_steps=max(steps, 1))
+    cfg = inputs.make_config(cfg_id, n=n, n_steps=warmup + steps + 1)
     sim, _ = oracle_from_config(cfg)
-    t0 = time.perf_counter()
-    sim.step(steps)
-    return (time.perf_counter() - t0) / steps, kspace.workers()
-
-
-def scale_to(n_from, n_to):
-    """Scale a per-step time by grid points times log2(grid points) (the 3D
-    FFTs dominate the oracle)."""
-    a, b = n_from ** 3, n_to ** 3
-    return (b * math.log2(b)) / (a * math.log2(a))
+    sim.step(warmup)
+    per = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        sim.step(1)
+        per.append(time.perf_counter() - t0)
+    return statistics.mean(per), per, kspace.workers()
 
 
 # ---------------------------------------------------------------- arms
@@ -268,17 +266,11 @@ def run_reference(args):
     if rank != 0:
         return
     cfg = inputs.make_config(args.config, n=args.n, n_steps=1)
-    n_full = cfg["shape"][0]
-    n_s = 128
-    for _ in range(args.warmup):
-        oracle_sample(args.config, n_s, 1)
-    per = []
-    for _ in range(args.steps):
-        s, cores = oracle_sample(args.config, n_s, 1)
-        per.append(s)
-    ms = 1e3 * statistics.mean(per) * scale_to(n_s, n_full)
-    sample = "config-%d recipe on a %d^3 grid, 1 step per timed step, scaled to %d^3 by N log2 N" % (
-        args.config, n_s, n_full)
+    sec, per, cores = oracle_timed(args.config, args.n, args.warmup, args.steps)
+    ms = 1e3 * sec
+    sample = ("FP64 oracle on the workload itself (%d^3 grid, medium, bowl source, sensors), %d warm-up "
+              "steps, then %d steps timed one by one (host set-up not timed); per-step %.1f-%.1f s"
+              % (cfg["shape"][0], args.warmup, args.steps, min(per), max(per)))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(ms, 3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
@@ -354,9 +346,15 @@ def run_ours(args):
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": ncu_traffic(dom, cfg["shape"]),
                      "algorithmic_bytes_per_launch": kb.get(dom), "launch_ms": round(dom_ms, 4),
-                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "byte_model": "every array the kernel must read or write, counted once; spectra as the "
+                                   "nx/2+1 columns used; rho0 read once and averaged to the staggered points "
+                                   "in the kernel",
+                     "frac_three_staggered_fields": (round((kb.get(dom, 0) + 2 * 4 * N) / (dom_ms * 1e-3) / 1e9 / peak, 4)
+                                                     if dom == "x_vel" and not np.isscalar(cfg["rho0"]) else None)},
         "step_roofline": {"bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (ms * 1e-3) / 1e9, 1),
-                          "frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4)},
+                          "frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4),
+                          "frac_78_fields": round(78 * 4 * N / (ms * 1e-3) / 1e9 / peak, 4)},
         "kernels_ms": {k: round(v, 4) for k, v in sorted(per_kernel.items(), key=lambda kv: -kv[1])},
         "clocks": clk,
         "device_status": status,
@@ -378,11 +376,11 @@ def run_ours(args):
     if not args.no_extra and world == 1:
         out["cufft_unfused"] = cufft_unfused(args, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
-        s, cores = oracle_sample(args.config, 128, 6)
-        cpu_ms = 1e3 * s * scale_to(128, cfg["shape"][0])
-        out["cpu_baseline"] = {"value": round(cpu_ms, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": "FP64 oracle, config-%d recipe on a 128^3 grid, 6 steps, "
-                                         "scaled to %d^3 by N log2 N" % (args.config, cfg["shape"][0])}
+        sec, per, cores = oracle_timed(args.config, args.n, 1, 2)
+        out["cpu_baseline"] = {"value": round(1e3 * sec, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "FP64 oracle on the workload itself (%d^3 grid, medium, bowl source, "
+                                         "sensors): 1 warm-up step, then 2 steps timed one by one (%.1f, %.1f s); "
+                                         "host set-up not timed" % (cfg["shape"][0], per[0], per[1])}
     if rank == 0:
         print(json.dumps(out))
     reps.close()
@@ -439,23 +437,37 @@ def _homogeneous(cfg):
 
 def adjoint_measure(kwgb, torch):
     """Forward + hand-written adjoint of the 256-element segmented bowl at 128^3
-    (600 steps, checkpoint every 50): time per step and device memory, beside
-    the plain forward step of the same problem."""
+    (600 steps, checkpoint every 50): time per step of each leg and device
+    memory, beside the plain forward step of the same problem and the
+    objective-only run (one forward run, no checkpoints)."""
     from paper_1408_4675_gb300.autograd import FocalProblem
     cfg = inputs.make_config(5)
     prob = FocalProblem(cfg, checkpoint_every=50)
+    nt = prob.n_steps
+
+    def per_step(t0):
+        return (time.perf_counter() - t0) * 1e3 / nt
     sim = prob.simulation(cfg["phases"], cfg["amps"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim.step(prob.n_steps)
+    sim.step(nt)
     sim.status()
-    fwd = (time.perf_counter() - t0) * 1e3 / prob.n_steps
+    fwd = per_step(t0)
     sim.close()
     t0 = time.perf_counter()
-    J, dphi, damp, _ = prob.value_and_grad(cfg["phases"], cfg["amps"])
-    tot = (time.perf_counter() - t0) * 1e3 / prob.n_steps
-    return {"workload": "segmented_bowl_256_elements_128^3", "steps": prob.n_steps, "checkpoint_every": 50,
-            "forward_ms_per_step": round(fwd, 4), "forward_plus_adjoint_ms_per_step": round(tot, 4),
+    prob.objective(cfg["phases"], cfg["amps"])
+    obj = per_step(t0)
+    t0 = time.perf_counter()
+    J, sim = prob.forward(cfg["phases"], cfg["amps"])
+    fwd_ck = per_step(t0)
+    t1 = time.perf_counter()
+    dphi, damp, _ = prob.backward(sim, cfg["phases"], cfg["amps"])
+    bwd = per_step(t1)
+    tot = per_step(t0)
+    return {"workload": "segmented_bowl_256_elements_128^3", "steps": nt, "checkpoint_every": 50,
+            "forward_ms_per_step": round(fwd, 4), "objective_only_ms_per_step": round(obj, 4),
+            "forward_with_checkpoints_ms_per_step": round(fwd_ck, 4), "reverse_ms_per_step": round(bwd, 4),
+            "forward_plus_adjoint_ms_per_step": round(tot, 4), "ratio_to_forward": round(tot / fwd, 3),
             "device_gb": round(prob.last_device_bytes / 1e9, 3), "J": J,
             "grad_norm_phases": float(np.linalg.norm(dphi))}
 

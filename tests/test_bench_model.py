@@ -1,8 +1,7 @@
 """Host logic of bench.py that the reported numbers rest on: the algorithmic
-byte model of each kernel (the roofline's numerator) and the scaling of the
-oracle's sampled time (the cpu_baseline)."""
+byte model of each kernel (the roofline's numerator), the L2 note and the
+clock record."""
 
-import math
 import os
 import sys
 
@@ -44,11 +43,6 @@ def test_byte_model_variants():
     assert scalar["x_eos"] == 3 * S + F and scalar["x_vel"] == 6 * S + 6 * F
     full = bench.kernel_bytes(_cfg(n, 3, sensors=((None, 3),)))
     assert full["x_eos"] - bench.kernel_bytes(_cfg(n, 3))["x_eos"] == 24 * n ** 3
-
-
-def test_oracle_sample_scaling_is_n_log_n():
-    assert math.isclose(bench.scale_to(128, 512), 64 * 27 / 21)
-    assert bench.scale_to(64, 64) == 1.0
 
 
 def test_l2_note_follows_the_field_size():

@@ -78,7 +78,7 @@ def test_reference_arm_under_two_rank_launcher():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port),
-           "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+           "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--grid", "32"]
     env = dict(os.environ, OMP_NUM_THREADS="2")
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -88,6 +88,7 @@ def test_reference_arm_under_two_rank_launcher():
     assert out["impl"] == "reference" and out["n_gpus"] == 2
     assert out["config"]["parallelism"] == "replicas"
     assert out["value"] > 0 and out["e2e"]["value"] == out["value"]
+    assert out["steps"] == 1 and "32^3" in out["cpu_baseline"]["sample"]
 
 
 if __name__ == "__main__":
