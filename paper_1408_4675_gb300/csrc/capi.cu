@@ -1334,6 +1334,8 @@ extern "C" int kwgb_adjoint_backward(kwgb_sim* sim, double* grad_out, int64_t gr
         if (int e = upload(sim, &d_rpts, rpts)) return e;
         if (int e = upload(sim, &d_rscale, rscale)) return e;
     }
+    int64_t* d_rev = static_cast<int64_t*>(dalloc(sim, sizeof(int64_t)));
+    if (!d_rev) return fail(sim, KWGB_ERR_OOM, "adjoint step counter");
     CK(cudaMemsetAsync(lam, 0, 8 * F, s));
     CK(cudaMemsetAsync(grad, 0, (size_t)std::max<int64_t>(rows, 1) * max_nt * sizeof(double), s));
     const GridC& g = sim->g;
@@ -1350,48 +1352,86 @@ extern "C" int kwgb_adjoint_backward(kwgb_sim* sim, double* grad_out, int64_t gr
     float2* sp[3] = {sim->T1, sim->T2, sim->T3};
     for (int a = 0; a < 3; ++a) ax.sp[a] = sp[a];
     float2* ab[3] = {sim->T1, sim->T2, nullptr};
-    for (int64_t c = nck - 1; c >= 0; --c) {
-        const int64_t n0 = c * K, n1 = std::min(n0 + K, n_steps);
-        // recompute the segment, keeping rho_xi^n and the d_xi of every step
-        if (int e = load_ck(sim, A.ck + (size_t)c * ck_bytes(sim), n0, s)) return e;
-        for (int64_t n = n0; n < n1; ++n) {
+    // One segment of len steps after its checkpoint is loaded (device step
+    // counter n0, reverse counter n0 + len - 1): recompute it, keeping rho_xi^n
+    // and the d_xi of every step, then step it backwards.  Every pointer
+    // depends only on the position in the segment, so a full segment can be
+    // captured once and replayed for the others.
+    auto segment = [&](cudaStream_t st, int64_t len) -> int {
+        for (int64_t k = 0; k < len; ++k) {
             for (int a = 0; a < 3; ++a) {
-                if (int e = copy_dev(sim, seg_rho(n - n0, a), sim->rho[a], F, s)) return e;
-                sim->adj_dout[a] = seg_d(n - n0, a);
+                if (int e = copy_dev(sim, seg_rho(k, a), sim->rho[a], F, st)) return e;
+                sim->adj_dout[a] = seg_d(k, a);
             }
-            const int e = launch_step(sim, s);
+            const int e = launch_step(sim, st);
             for (int a = 0; a < 3; ++a) sim->adj_dout[a] = nullptr;
             if (e) return e;
         }
         for (int a = 0; a < 3; ++a)
-            if (int e = copy_dev(sim, seg_rho(n1 - n0, a), sim->rho[a], F, s)) return e;
-        // reverse steps of the segment
-        for (int64_t n = n1 - 1; n >= n0; --n) {
-            const int64_t k = n - n0;
+            if (int e = copy_dev(sim, seg_rho(len, a), sim->rho[a], F, st)) return e;
+        cudaStream_t s = st;                                                  // for LK
+        for (int64_t k = len - 1; k >= 0; --k) {
             for (int a = 0; a < 3; ++a) {
                 ax.rho_before[a] = seg_rho(k, a);
                 ax.rho_after[a] = seg_rho(k + 1, a);
                 ax.d[a] = seg_d(k, a);
             }
-            LK(launch_adj_obj(n_obj, A.d_obj, A.pobj + n * n_obj, A.w, ax.lam_p, s));
-            if (absorbing) {                                                      // Eq. 8 backwards
+            LK(launch_adj_obj(n_obj, A.d_obj, A.pobj, d_rev, A.w, ax.lam_p, s));
+            if (absorbing) {                                                  // Eq. 8 backwards
                 LK(launch_adj_x_absprep(g, sim->md, ax, s));
                 LK(ypass(sim, -1, ab, ab, 2, s));
                 LK(zop(sim, Z_ABS, ab, ab, s));
                 LK(ypass(sim, +1, ab, ab, 2, s));
             }
-            LK(launch_adj_x_dens(g, sim->md, ax, s));                            // Eqs. 6, 4d backwards
-            LK(launch_adj_src((int)rows, d_rptr, d_rpts, d_rscale, d_rnt, ax.lam_src, sim->md, grad, max_nt, n, s));
-            LK(ypass(sim, -1, sp, sp, 3, s));                                     // transpose of Eq. 4c
+            LK(launch_adj_x_dens(g, sim->md, ax, s));                        // Eqs. 6, 4d backwards
+            LK(launch_adj_src((int)rows, d_rptr, d_rpts, d_rscale, d_rnt, ax.lam_src, sim->md, grad, max_nt, d_rev, s));
+            LK(ypass(sim, -1, sp, sp, 3, s));                                 // transpose of Eq. 4c
             LK(zop(sim, Z_DIV_FWD, sp, sp, s));
             LK(ypass(sim, +1, sp, sp, 3, s));
-            LK(launch_adj_x_vel(g, sim->md, ax, s));                             // Eq. 4b backwards
-            LK(ypass(sim, -1, sp, sp, 3, s));                                     // transpose of Eq. 4a
+            LK(launch_adj_x_vel(g, sim->md, ax, s));                         // Eq. 4b backwards
+            LK(ypass(sim, -1, sp, sp, 3, s));                                 // transpose of Eq. 4a
             LK(zop(sim, Z_DIV, sp, sp, s));
             LK(ypass(sim, +1, sp, sp, 3, s));
             LK(launch_adj_x_p(g, sim->md, ax, s));
+            LK(launch_adj_retreat(d_rev, s));
+        }
+        return KWGB_OK;
+    };
+    cudaGraphExec_t seg_exec = nullptr;
+    bool direct_done = false;                  // a full segment has run directly (one-time set-up done)
+    int64_t seg_launches = 0;
+    for (int64_t c = nck - 1; c >= 0; --c) {
+        const int64_t n0 = c * K, n1 = std::min(n0 + K, n_steps);
+        if (int e = load_ck(sim, A.ck + (size_t)c * ck_bytes(sim), n0, s)) return e;
+        const int64_t nr = n1 - 1;
+        CK(cudaMemcpyAsync(d_rev, &nr, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));          // the host value nr goes out of scope
+        if (n1 - n0 == K && direct_done && !seg_exec && sim->cap) {
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(sim->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const int64_t l0 = sim->launches;
+                const std::string err = sim->err;
+                const int e = segment(sim->cap, K);
+                const cudaError_t ce = cudaStreamEndCapture(sim->cap, &graph);
+                seg_launches = sim->launches - l0;
+                sim->launches = l0;
+                sim->err = err;
+                if (e != KWGB_OK || ce != cudaSuccess || !graph ||
+                    cudaGraphInstantiate(&seg_exec, graph, 0) != cudaSuccess)
+                    seg_exec = nullptr;
+                if (graph) cudaGraphDestroy(graph);
+            }
+            cudaGetLastError();
+        }
+        if (n1 - n0 == K && seg_exec) {
+            CK(cudaGraphLaunch(seg_exec, s));
+            sim->launches += seg_launches;
+        } else {
+            if (int e = segment(s, n1 - n0)) return e;
+            if (n1 - n0 == K) direct_done = true;
         }
     }
+    if (seg_exec) cudaGraphExecDestroy(seg_exec);
     // ---- put back the forward end state and the sensors
     if (int e = load_ck(sim, A.fin, n_steps, s)) return e;
     {

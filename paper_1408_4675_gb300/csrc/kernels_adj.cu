@@ -243,11 +243,14 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) adj_x_p_kernel(c
 
 __device__ __forceinline__ float medv(const float* f, float s, int64_t i) { return f ? f[i] : s; }
 
-__global__ void adj_obj_kernel(int64_t n, const int64_t* __restrict__ idx, const float* __restrict__ p,
-                               double weight, float* lam_p) {
+// The reverse step's index n is read from the device counter nrev (so that a
+// captured segment of reverse steps serves every segment), and lowered by
+// adj_retreat_kernel at the end of each reverse step.
+__global__ void adj_obj_kernel(int64_t n_obj, const int64_t* __restrict__ idx, const float* __restrict__ pobj,
+                               const int64_t* __restrict__ nrev, double weight, float* lam_p) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const float v = p[k];
+    if (k >= n_obj) return;
+    const float v = pobj[*nrev * n_obj + k];                  // p^{n+1} at objective point k
     const float sgn = v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f);   // d|p|/dp
     lam_p[idx[k]] += (float)(weight * sgn);
 }
@@ -255,8 +258,9 @@ __global__ void adj_obj_kernel(int64_t n, const int64_t* __restrict__ idx, const
 __global__ void adj_src_kernel(int rows, const int32_t* __restrict__ row_ptr, const int64_t* __restrict__ pts,
                                const float* __restrict__ scale, const int32_t* __restrict__ nt,
                                const float* __restrict__ lam_src, Medium md, double* grad, int64_t stride,
-                               int64_t n) {
+                               const int64_t* __restrict__ nrev) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = *nrev;
     if (r >= rows || n >= nt[r]) return;
     double acc = 0.0;
     for (int k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
@@ -266,6 +270,7 @@ __global__ void adj_src_kernel(int rows, const int32_t* __restrict__ row_ptr, co
     grad[r * stride + n] += acc;
 }
 
+__global__ void adj_retreat_kernel(int64_t* nrev) { *nrev -= 1; }
 
 cudaError_t launch_adj_x_absprep(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s) {
     AdjXK K{g, m, a};
@@ -313,18 +318,23 @@ cudaError_t launch_adj_x_p(const GridC& g, const Medium& m, const AdjX& a, cudaS
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_adj_obj(int64_t n, const int64_t* idx, const float* p, double weight, float* lam_p,
-                           cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    adj_obj_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, idx, p, weight, lam_p);
+cudaError_t launch_adj_obj(int64_t n_obj, const int64_t* idx, const float* pobj, const int64_t* nrev, double weight,
+                           float* lam_p, cudaStream_t s) {
+    if (n_obj <= 0) return cudaSuccess;
+    adj_obj_kernel<<<(unsigned)((n_obj + 255) / 256), 256, 0, s>>>(n_obj, idx, pobj, nrev, weight, lam_p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_src(int rows, const int32_t* row_ptr, const int64_t* pts, const float* scale,
                            const int32_t* nt, const float* lam_src, const Medium& m, double* grad,
-                           int64_t stride, int64_t n, cudaStream_t s) {
+                           int64_t stride, const int64_t* nrev, cudaStream_t s) {
     if (rows <= 0) return cudaSuccess;
-    adj_src_kernel<<<(rows + 127) / 128, 128, 0, s>>>(rows, row_ptr, pts, scale, nt, lam_src, m, grad, stride, n);
+    adj_src_kernel<<<(rows + 127) / 128, 128, 0, s>>>(rows, row_ptr, pts, scale, nt, lam_src, m, grad, stride, nrev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_retreat(int64_t* nrev, cudaStream_t s) {
+    adj_retreat_kernel<<<1, 1, 0, s>>>(nrev);
     return cudaGetLastError();
 }
 

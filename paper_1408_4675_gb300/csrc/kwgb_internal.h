@@ -200,12 +200,14 @@ cudaError_t launch_adj_x_dens(const GridC& g, const Medium& m, const AdjX& a, cu
 cudaError_t launch_adj_x_vel(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
 // lambda_p = -(C2R sp[0] + C2R sp[1] + C2R sp[2])
 cudaError_t launch_adj_x_p(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
-// lambda_p[idx_k] += weight * sign(p_k) for the objective points
-cudaError_t launch_adj_obj(int64_t n, const int64_t* idx, const float* p, double weight, float* lam_p,
-                           cudaStream_t s);
-// per signal row r: grad[r * stride + n] += sum over its points of lambda_src * scale / c0 (n < nt_r)
+// lambda_p[idx_k] += weight * sign(p^{n+1}_k), n = *nrev, samples pobj[n * n_obj + k]
+cudaError_t launch_adj_obj(int64_t n_obj, const int64_t* idx, const float* pobj, const int64_t* nrev, double weight,
+                           float* lam_p, cudaStream_t s);
+// per signal row r: grad[r * stride + n] += sum over its points of lambda_src * scale / c0 (n = *nrev < nt_r)
 cudaError_t launch_adj_src(int rows, const int32_t* row_ptr, const int64_t* pts, const float* scale,
                            const int32_t* nt, const float* lam_src, const Medium& m, double* grad,
-                           int64_t stride, int64_t n, cudaStream_t s);
+                           int64_t stride, const int64_t* nrev, cudaStream_t s);
+// *nrev -= 1
+cudaError_t launch_adj_retreat(int64_t* nrev, cudaStream_t s);
 
 }  // namespace kwgb
