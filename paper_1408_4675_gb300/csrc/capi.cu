@@ -23,6 +23,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/kwgb.h"
+#include "fft_tc5.cuh"
 #include "kwgb_internal.h"
 
 using namespace kwgb;
@@ -275,6 +276,53 @@ extern "C" int kwgb_set_allocator(kwgb_sim* sim, void* (*alloc)(size_t, void*),
 }
 
 // ------------------------------------------------------------------ medium
+// One 64 x 64 operand of the tensor-core form (layout tc5_koff): `blocks`
+// copies on the diagonal of the L-point forward DFT in real form (row
+// 2k + r, column 2b + s; L = 64 / (2 blocks)), split into hi = round(a) and
+// lo = round(a - hi) in float16 (prec 2) or bfloat16 (prec 1), generated in
+// float64.
+static void tc5_dft_operand(int prec, int L, uint16_t* hi, uint16_t* lo) {
+    for (int m = 0; m < 64; ++m)
+        for (int k = 0; k < 64; ++k) {
+            double v = 0.0;
+            if (m / (2 * L) == k / (2 * L)) {
+                const int kk = (m % (2 * L)) / 2, b = (k % (2 * L)) / 2;
+                const double th = -2.0 * kPi * (double)((kk * b) % L) / (double)L;
+                const int r = m & 1, c = k & 1;
+                // (x_re + i x_im)(cos th + i sin th): re row [cos, -sin], im row [sin, cos]
+                v = r == 0 ? (c == 0 ? std::cos(th) : -std::sin(th)) : (c == 0 ? std::sin(th) : std::cos(th));
+            }
+            uint16_t h, l;
+            if (prec == 2) {
+                const __half hh = __float2half_rn((float)v);
+                const __half ll = __float2half_rn((float)(v - (double)__half2float(hh)));
+                std::memcpy(&h, &hh, 2);
+                std::memcpy(&l, &ll, 2);
+            } else {
+                const __nv_bfloat16 hh = __float2bfloat16_rn((float)v);
+                const __nv_bfloat16 ll = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hh)));
+                std::memcpy(&h, &hh, 2);
+                std::memcpy(&l, &ll, 2);
+            }
+            const int o = tc5_koff(m, k) / 2;
+            hi[o] = h;
+            lo[o] = l;
+        }
+}
+
+// The operands of the tcgen05 passes: the 32-point DFT (stage 1), then the
+// stage-2 operand of y lines and of z lines (32 / n1 copies of the n1-point
+// DFT, n1 = n / 32; unused for n < 64); each as hi then lo.
+static void tc5_operands(int prec, int ny, int nz, std::vector<uint32_t>& out) {
+    out.assign(6 * TC5_A_WORDS, 0u);
+    uint16_t* p = reinterpret_cast<uint16_t*>(out.data());
+    const int per = TC5_A_BYTES / 2;
+    tc5_dft_operand(prec, 32, p, p + per);
+    const int n1[2] = {ny / 32, nz / 32};
+    for (int i = 0; i < 2; ++i)
+        if (n1[i] >= 2) tc5_dft_operand(prec, n1[i], p + (2 + 2 * i) * per, p + (3 + 2 * i) * per);
+}
+
 static int build_tables(kwgb_sim* sim) {
     const kwgb_grid_desc& d = sim->d;
     GridC& g = sim->g;
@@ -312,6 +360,13 @@ static int build_tables(kwgb_sim* sim) {
         if (int e = upload(sim, &df2, fs)) return e;
         g.t.pml[a] = df1;
         g.t.pml_sg[a] = df2;
+    }
+    if (g.mixed) {
+        std::vector<uint32_t> a;
+        tc5_operands(g.mixed, (int)d.ny, (int)d.nz, a);
+        uint32_t* da;
+        if (int e = upload(sim, &da, a)) return e;
+        g.t.tc5a = da;
     }
     return KWGB_OK;
 }

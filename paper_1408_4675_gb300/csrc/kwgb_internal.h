@@ -25,6 +25,9 @@ struct Tables {
     const float2* dfz;
     const float* pml[3];      // PML factor exp(-a dt / 2) on the regular grid, per axis
     const float* pml_sg[3];   // ... on the staggered grid i + 1/2
+    // tensor-core forms: 64 x 64 DFT operands (hi, lo; fft_tc5.cuh layout) of the
+    // radix-32 stage, then of the second stage of y lines, then of z lines
+    const uint32_t* tc5a;
 };
 
 struct GridC {

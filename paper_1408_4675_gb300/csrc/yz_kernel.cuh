@@ -19,8 +19,11 @@
 // inverse z FFT, store.  It plays the role of the paper's transposed-space
 // spectral multiply (Sec. 3.2): the spectrum does not return to HBM between
 // the forward and the inverse transform along z.
+#include <algorithm>
+
 #include "fft_core.cuh"
 #include "fft_tc.cuh"
+#include "fft_tc5.cuh"
 #include "kwgb_internal.h"
 #include "tma.cuh"
 
@@ -53,18 +56,32 @@ struct TileSmem {
 template <int LOGN, bool ISY, int MIXED = 0>
 struct TShape {
     static constexpr int N = 1 << LOGN;
+    // tensor-core form: lines of 64 points and more run on tcgen05 (fft_tc5.cuh),
+    // shorter ones on mma.sync (fft_tc.cuh)
+    static constexpr bool TC5 = MIXED != 0 && LOGN >= 6;
     // z: E = 8 keeps the operator pass spill-free at two CTAs per SM; 1024-point
-    // lines take E = 16 so that a tile stays 8 columns (64-byte TMA rows) wide
-    static constexpr int E = ISY ? (LOGN >= 8 ? 16 : 8) : (LOGN >= 10 ? 16 : 8);
+    // lines take E = 16 so that a tile stays 8 columns (64-byte TMA rows) wide.
+    // tcgen05 form: 16 values per thread (8 for 64-point lines, which need the
+    // four warps of a tensor-memory read-back) and tiles of at most 256
+    // threads (4 columns for 1024-point lines), so that two CTAs share an SM
+    static constexpr int E = TC5 ? (LOGN >= 7 ? 16 : 8) : (ISY ? (LOGN >= 8 ? 16 : 8) : (LOGN >= 10 ? 16 : 8));
     static constexpr int TL = N / E;
-    static constexpr int MAXT = (ISY && MIXED && LOGN == 9) ? 256 : 512;
+    static constexpr int MAXT = TC5 ? 256 : ((ISY && MIXED && LOGN == 9) ? 256 : 512);
     static constexpr int CX = (MAXT / TL) >= 16 ? 16 : (MAXT / TL);
     static constexpr int THREADS = CX * TL;
     static constexpr int BOX = N < 256 ? N : 256;
     static constexpr int NBOX = N / BOX;
     static constexpr int STAGE = N * CX;                       // complex elements per stage
-    // two TMA stages, plus the scratch exchange buffer of the float32 passes
-    static constexpr int smem(int mixed) { return (mixed ? 2 : 3) * STAGE * (int)sizeof(float2) + 64; }
+    static constexpr int NST = TC5 ? 1 : 2;                    // TMA stages (tcgen05: one, two CTAs per SM)
+    static constexpr int NC = (N / 32) * CX;                   // product columns of a tile
+    static constexpr int TC5_TMEM = tc5_tmem_cols(NC);
+    static constexpr int TC5_A = (LOGN == 10 ? 2 : 4) * TC5_A_BYTES;   // A operands (one set for 1024 points)
+    // two TMA stages, plus the scratch exchange buffer of the float32 passes, or
+    // (tcgen05) one stage, 1 KB of barriers, the A operands and the B operand (hi, lo)
+    static constexpr int smem(int mixed) {
+        return TC5 ? STAGE * (int)sizeof(float2) + 1024 + TC5_A + 2 * NC * 128
+                   : (mixed ? 2 : 3) * STAGE * (int)sizeof(float2) + 64;
+    }
 };
 
 struct alignas(64) YZK {
@@ -117,7 +134,7 @@ __device__ __forceinline__ float2* out_ptr(const YZK& a, int i) {
 // float32 register passes, or (MIXED) through the tile in shared memory.
 template <int LOGN, int E, int CX, int THREADS, int MIXED>
 __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX, MIXED == 0>& S, float2* tile,
-                                             const float2* __restrict__ tw, TcColMax& cmx) {
+                                             const float2* __restrict__ tw, TcColMax& cmx, Tc5& t5) {
     constexpr int TL = (1 << LOGN) / E;
     if constexpr (MIXED == 0) {
         line_fft<LOGN, E, +1>(v, j, S, tw);
@@ -132,9 +149,15 @@ __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX,
             tc_colmax_deposit<CX>(mx, cmx);
         }
         __syncthreads();
-        tile_fft_tc<LOGN, CX, +1, THREADS, MIXED, false>(tile, tw, cmx);
+        if constexpr (LOGN >= 6) {
+            tile_fft_tc5<LOGN, CX, +1, THREADS, MIXED, false>(tile, t5, tw, cmx);
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = tile[TcResult<LOGN, CX>::idx(j + TL * m, S.c)];
+            for (int m = 0; m < E; ++m) v[m] = tile[(j + TL * m) * CX + S.c];
+        } else {
+            tile_fft_tc<LOGN, CX, +1, THREADS, MIXED, false>(tile, tw, cmx);
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = tile[TcResult<LOGN, CX>::idx(j + TL * m, S.c)];
+        }
     }
 }
 
@@ -145,6 +168,7 @@ __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX,
 // which costs less than the idle barrier time of one CTA per SM).
 template <int LOGN, int OP, int MIXED>
 constexpr int yz_min_blocks() {
+    if (MIXED && LOGN >= 6) return 2;                 // tcgen05 form: two CTAs per SM
     if (OP < 2) return (MIXED && LOGN == 9) ? 3 : 1;
     if (LOGN >= 10) return 1;
     return (MIXED && LOGN != 9) ? 1 : 2;
@@ -159,8 +183,9 @@ yz_kernel(const __grid_constant__ YZK a) {
     extern __shared__ __align__(128) float2 smem[];
     __shared__ int abort_flag;
     __shared__ unsigned int colmax[32];              // column maxima of the float16-split form (2 buffers)
+    constexpr int NST = Sh::NST;
     float2* scratch = smem + 2 * STAGE;             // float32 exchanges (not used by MIXED)
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (MIXED ? 2 : 3) * STAGE);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (Sh::TC5 ? 1 : (MIXED ? 2 : 3)) * STAGE);
     const GridC& g = a.g;
     const int tid = threadIdx.x;
     const int c = tid % CX, j = tid / CX;
@@ -174,15 +199,42 @@ yz_kernel(const __grid_constant__ YZK a) {
     const int my = items > (int)blockIdx.x ? (items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int Q = my * L;
 
+    constexpr bool TC5 = Sh::TC5;
+    Tc5 t5{};
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
+    if constexpr (TC5) {
+        // A operands from global memory (stage 1, then this axis's stage 2), the
+        // product barrier, the accumulator in tensor memory
+        unsigned char* base = reinterpret_cast<unsigned char*>(bar);
+        t5.bar = bar + 2;
+        t5.a1 = base + 1024;
+        t5.a2 = LOGN == 10 ? t5.a1 : t5.a1 + 2 * TC5_A_BYTES;
+        t5.b = t5.a1 + Sh::TC5_A;
+        const uint4* s1 = reinterpret_cast<const uint4*>(g.t.tc5a);
+        const uint4* s2 = reinterpret_cast<const uint4*>(g.t.tc5a + (ISY ? 2 : 4) * TC5_A_WORDS);
+        for (int i = tid; i < 2 * TC5_A_BYTES / 16; i += Sh::THREADS) {
+            reinterpret_cast<uint4*>(t5.a1)[i] = __ldg(s1 + i);
+            if (LOGN != 10) reinterpret_cast<uint4*>(t5.a2)[i] = __ldg(s2 + i);
+        }
+        if (tid < 32) tc5_alloc(tslot, Sh::TC5_TMEM);
+        t5.flag = a.flag;
+        t5.ok = true;
+    }
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        if (TC5) mbar_init(t5.bar, 1);
         fence_mbar_init();
         abort_flag = 0;
     }
     if (tid < 32) colmax[tid] = 0u;
     TcColMax cmx{colmax, 0};
+    if (TC5) tc5_fence_before();
     __syncthreads();
+    if constexpr (TC5) {
+        tc5_fence_after();
+        t5.tmem = *tslot;
+    }
 
     auto issue = [&](int q) {                 // thread 0 only
         const int item = (int)blockIdx.x + (q / L) * (int)gridDim.x;
@@ -191,8 +243,8 @@ yz_kernel(const __grid_constant__ YZK a) {
         const int line = (item / nchunk) % lines;
         const int mi = ISY ? item / (nchunk * lines) : (l == 0 ? a.load_comp[0] : (l == 1 ? a.load_comp[1] : a.load_comp[2]));
         const CUtensorMap* map = mi == 0 ? &a.map[0] : (mi == 1 ? &a.map[1] : &a.map[2]);
-        float2* dst = smem + (q & 1) * STAGE;
-        uint64_t* b = &bar[q & 1];
+        float2* dst = smem + (q % NST) * STAGE;
+        uint64_t* b = &bar[q % NST];
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(b, STAGE * (uint32_t)sizeof(float2) + g.wait_fault_tx);
 #pragma unroll
@@ -209,9 +261,9 @@ yz_kernel(const __grid_constant__ YZK a) {
     for (int m = 0; m < E; ++m) { kap[m] = 0.f; lg[m] = 0.f; }
 
     for (int q = 0; q < Q; ++q) {
-        const int s = q & 1;
-        if (tid == 0 && q + 1 < Q) issue(q + 1);
-        const bool ok = mbar_wait_bounded(&bar[s], (q >> 1) & 1, a.flag);
+        const int s = q % NST;
+        if (NST == 2 && tid == 0 && q + 1 < Q) issue(q + 1);
+        const bool ok = mbar_wait_bounded(&bar[s], (q / NST) & 1, a.flag);
         if (!ok) abort_flag = 1;
         const int item = (int)blockIdx.x + (q / L) * (int)gridDim.x;
         const int l = q % L;
@@ -222,9 +274,13 @@ yz_kernel(const __grid_constant__ YZK a) {
         TileSmem<CX, MIXED == 0> S{smem + s * STAGE, scratch, c};
         constexpr int THREADS = Sh::THREADS;
         float2 v[E];
-        if constexpr (MIXED != 0)
+        if constexpr (TC5) {
+            tile_fft_tc5<LOGN, CX, (ISY ? (OP == OP_Y_FWD ? -1 : +1) : -1), THREADS, MIXED>(smem + s * STAGE, t5,
+                                                                                          g.t.tw, cmx);
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = smem[s * STAGE + (j + TL * m) * CX + c];
+        } else if constexpr (MIXED != 0) {
             tile_fft_tc<LOGN, CX, (ISY ? (OP == OP_Y_FWD ? -1 : +1) : -1), THREADS, MIXED>(smem + s * STAGE, g.t.tw, cmx);
-        if constexpr (MIXED != 0) {
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = smem[s * STAGE + TcResult<LOGN, CX>::idx(j + TL * m, c)];
         } else {
@@ -280,7 +336,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                 float2* o1 = a.out[1];
                 float2* o2 = a.out[2];
                 if (o0 != nullptr || o1 != nullptr) {           // uniform
-                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, cmx);
+                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, cmx, t5);
                     if (valid) {
 #pragma unroll
                         for (int m = 0; m < E; ++m) {
@@ -291,7 +347,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                     }
                 }
                 if (o2 != nullptr) {
-                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(w, j, S, smem + s * STAGE, g.t.tw, cmx);
+                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(w, j, S, smem + s * STAGE, g.t.tw, cmx, t5);
                     if (valid) {
 #pragma unroll
                         for (int m = 0; m < E; ++m) __stcs(o2 + off + (size_t)(j + TL * m) * es, w[m]);
@@ -307,7 +363,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                     if (OP == OP_Z_DIV) d = make_float2(-d.x, d.y);   // Eq. 4c: i k e^{-ikd/2}
                     v[m] = cscale(cmul(v[m], d), kap[m]);            // OP_Z_DIV_FWD: Eq. 4a's operator
                 }
-                inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, cmx);
+                inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, cmx, t5);
                 if (valid) {
                     float2* out = out_ptr(a, xi) + off;
 #pragma unroll
@@ -321,7 +377,7 @@ yz_kernel(const __grid_constant__ YZK a) {
                     const float f = lg[m] > -INFINITY ? exp2f(e * lg[m]) * cst : 0.f;   // k^{y-2} / k^{y-1}, 0 at k = 0
                     v[m] = cscale(v[m], f);
                 }
-                inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, cmx);
+                inverse_tile<LOGN, E, CX, THREADS, MIXED>(v, j, S, smem + s * STAGE, g.t.tw, cmx, t5);
                 if (valid) {
                     float2* out = out_ptr(a, t) + off;
 #pragma unroll
@@ -329,11 +385,22 @@ yz_kernel(const __grid_constant__ YZK a) {
                 }
             }
         }
-        __syncthreads();                          // stage s is free for the load of q + 2
+        if (TC5 && !t5.ok && tid == 0) abort_flag = 1;
+        __syncthreads();                          // stage s is free for the load of q + NST
         if (abort_flag) {
-            if (tid == 0 && q + 1 < Q) mbar_wait_bounded(&bar[(q + 1) & 1], ((q + 1) >> 1) & 1, a.flag);
-            return;
+            if (NST == 2 && tid == 0 && q + 1 < Q) mbar_wait_bounded(&bar[(q + 1) & 1], ((q + 1) >> 1) & 1, a.flag);
+            break;
         }
+        if (NST == 1 && tid == 0 && q + 1 < Q) issue(q + 1);
+    }
+    if constexpr (TC5) {
+        // a product whose wait ran out gets one more bounded wait before its
+        // accumulator is freed
+        if (!t5.ok && tid == 0) mbar_wait_bounded(t5.bar, t5.phase ^ 1u, a.flag);
+        tc5_fence_before();
+        __syncthreads();
+        tc5_fence_after();
+        if (tid < 32) tc5_dealloc(t5.tmem, Sh::TC5_TMEM);
     }
 }
 
@@ -346,8 +413,28 @@ inline cudaError_t launch_t(const YZK& a, int items, cudaStream_t s) {
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::smem(MIXED));
         if (e != cudaSuccess) return e;
+        if (Sh::TC5) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+            if (e != cudaSuccess) return e;
+        }
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Sh::THREADS, Sh::smem(MIXED));
         if (e != cudaSuccess) return e;
+        if (Sh::TC5) {
+            // residency from the kernel's registers and shared memory (the query
+            // has returned less than the hardware holds for the tensor-core form);
+            // each resident CTA holds TC5_TMEM of the 512 tensor-memory columns
+            cudaFuncAttributes fa;
+            int dev = 0, smem_sm = 0, regs_sm = 0;
+            if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess) {
+                const int per_block = Sh::smem(MIXED) + (int)fa.sharedSizeBytes + 1024;
+                const int regs = ((fa.numRegs + 7) / 8) * 8 * Sh::THREADS;
+                int m = std::min(smem_sm / per_block, regs_sm / std::max(regs, 1));
+                m = std::min(m, 512 / Sh::TC5_TMEM);
+                per_sm = std::max(per_sm, m);
+            }
+        }
         if (per_sm < 1) per_sm = 1;
     }
     int grid = per_sm * a.g.num_sms;
