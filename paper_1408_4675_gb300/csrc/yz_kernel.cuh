@@ -64,7 +64,7 @@ struct TShape {
     // tcgen05 form: 16 values per thread (8 for 64-point lines, which need the
     // four warps of a tensor-memory read-back) and tiles of at most 256
     // threads (4 columns for 1024-point lines), so that two CTAs share an SM
-    static constexpr int E = TC5 ? (LOGN >= 7 ? 16 : 8) : (ISY ? (LOGN >= 8 ? 16 : 8) : (LOGN >= 10 ? 16 : 8));
+    static constexpr int E = TC5 ? ((LOGN == 10 || LOGN == 7) ? 16 : 8) : (ISY ? (LOGN >= 8 ? 16 : 8) : (LOGN >= 10 ? 16 : 8));
     static constexpr int TL = N / E;
     static constexpr int MAXT = TC5 ? 256 : ((ISY && MIXED && LOGN == 9) ? 256 : 512);
     static constexpr int CX = (MAXT / TL) >= 16 ? 16 : (MAXT / TL);
@@ -168,7 +168,7 @@ __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX,
 // which costs less than the idle barrier time of one CTA per SM).
 template <int LOGN, int OP, int MIXED>
 constexpr int yz_min_blocks() {
-    if (MIXED && LOGN >= 6) return 2;                 // tcgen05 form: two CTAs per SM
+    if (MIXED && LOGN >= 6) return (LOGN == 8 || LOGN == 9) ? 3 : 2;   // tcgen05 form: two or three CTAs per SM
     if (OP < 2) return (MIXED && LOGN == 9) ? 3 : 1;
     if (LOGN >= 10) return 1;
     return (MIXED && LOGN != 9) ? 1 : 2;
