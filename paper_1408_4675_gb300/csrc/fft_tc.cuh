@@ -1,4 +1,7 @@
-// Split-precision tensor-core form of the strided FFT passes.
+// Split-precision tensor-core form of the strided FFT passes of 16- and
+// 32-point lines (mma.sync; lines of 64 points and more run on tcgen05,
+// fft_tc5.cuh, which reuses the operand splits and float16 column scales
+// defined here).
 //
 // A tile (CX columns x N points, layout [e][c] in shared memory) is
 // transformed in place.  Every radix-8 Stockham stage is written as a real
@@ -14,17 +17,15 @@
 // PREC 2 uses float16 hi + lo instead (11 + 11 significant bits, relative
 // residue 2^-22): float16 has a narrow exponent range, so each column is
 // scaled by a power of two (exact) that brings its largest input to [32, 64);
-// 8-point stages grow values at most 8x, so a 512-point column stays below
-// the float16 maximum 65504; outputs are scaled back before they are stored.
+// 8-point stages grow values at most 8x, so a column stays far below the
+// float16 maximum 65504; outputs are scaled back before they are stored.
 // A remaining radix-2 or radix-4 stage runs in float32 on the CUDA cores.
 // Each thread reads its B fragment (two complex inputs of one butterfly)
 // straight from the Stockham input positions, applies the stage twiddles, and
 // writes its D fragment (one complex output of two butterflies) straight to
-// the Stockham output positions, so no extra shuffles are needed.  For 512-
-// and 1024-point lines the stages of strides 8 and 64 share one pass
-// (tc_stage8x8: the accumulator fragment of the first product is the operand
-// fragment of the second).  Between passes the tile is XOR-swizzled so that
-// the accesses are free of bank conflicts (TcSwz, TcXor).
+// the Stockham output positions, so no extra shuffles are needed.  Between
+// passes the tile is XOR-swizzled so that the accesses are free of bank
+// conflicts (TcSwz, TcXor).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -161,25 +162,6 @@ struct TcXor {
 template <int CX>
 using TcPlain = TcXor<CX, 0u, 0u, 0u, 0u, 0u>;
 
-// Layouts of the 512- and 1024-point transforms (radix-8 stage of stride 1,
-// then the strides 8 and 64 in one pass, see tc_stage8x8).  With G = log2 N - 6
-// and T = log2 N - 2:
-//   TcMid (written by the first stage, read by the fused pass):
-//     H0 = b0 ^ bG, H1 = b(G+1), H2 = bT, and H3 = b1 ^ b(T+1) (16 columns)
-//     or P = b1 ^ b(T+1) (8 columns).  The first stage's writes vary row bits
-//     0, 1 and column bits 1, 2 within a half-warp, the fused pass's reads row
-//     bits G, G+1, T, T+1 in one column: both meet 16 distinct bank pairs.
-//   TcOut (written by the fused pass): H = (b4, b5, b6) and H3 = b7 or P = b7.
-//     The fused pass's writes vary row bits 4..7 in one column; the readers
-//     after it (the radix-2 float32 stage, the kernel's copy-out) vary the
-//     column and row bit 0 only, which no mask holds.
-// (Every access of the three tile shapes used was checked by enumeration.)
-template <int LOGN, int CX>
-using TcMid = TcXor<CX, 1u | (1u << (LOGN - 6)), 1u << (LOGN - 5), 1u << (LOGN - 2),
-                    CX == 16 ? (2u | (1u << (LOGN - 1))) : 0u, CX == 8 ? (2u | (1u << (LOGN - 1))) : 0u>;
-template <int CX>
-using TcOut = TcXor<CX, 1u << 4, 1u << 5, 1u << 6, CX == 16 ? (1u << 7) : 0u, CX == 8 ? (1u << 7) : 0u>;
-
 // Float16-split column scale from the bits of the column maximum m (a
 // non-negative float, biased exponent ex): 2^k with k = 132 - ex, so that
 // m 2^k lies in [32, 64), or 2^-k when `inverse`; k is clamped to [-100, 100]
@@ -298,90 +280,6 @@ __device__ __forceinline__ void f32_stage(float2* buf, const float2* __restrict_
     __syncthreads();
 }
 
-// The radix-8 stages of strides 8 and 64 of a 512- or 1024-point transform in
-// one pass through shared memory.  A group is one tile column c and one
-// B0 < N/64 (alpha = B0 % 8, beta = B0 / 8).  Stage a (stride 8) takes the
-// butterflies B0 + r N/64, r = 0..7, as the eight B columns of one product;
-// stage b (stride 64) takes the butterflies 64 beta + 8 q + alpha, q = 0..7,
-// whose input r is output q of stage-a butterfly r.  The m16n8k16 accumulator
-// leaves output g of B columns 2t, 2t + 1 in lane (g, t), and the next B
-// fragment of that lane is inputs 2t, 2t + 1 of B column g: the same values.
-// So the 64-point sub-transforms stay in registers; between the two products
-// only the stage-b twiddles are applied (and the operands split again).
-// Reads layout LI (TcMid), writes LO (TcOut).  Float16-split: the column scale
-// is applied once before stage a and removed after stage b (the values grow at
-// most 64x in between, which float16 holds at the [32, 64) input scale).
-template <int N, int CX, int DIR, int THREADS, int PREC, class LI, class LO>
-__device__ __forceinline__ void tc_stage8x8(float2* buf, const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                            const float2* __restrict__ tw, const unsigned int* colmax) {
-    static_assert(N == 512 || N == 1024, "strides 8 and 64 of a 512- or 1024-point line");
-    constexpr int WARPS = THREADS / 32;
-    constexpr int GROUPS = CX * (N / 64) / WARPS;            // groups per warp
-    static_assert((CX * (N / 64)) % WARPS == 0, "tile / warp split");
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    // per-lane parts of the layouts (the parts of a row occupy disjoint bits):
-    // reads rows B0 + g N/64 + (2t + d) N/8, writes rows 512 beta + alpha + 8 (2t + i) + 64 g
-    const int rg = g * (N / 64), r0 = (2 * t) * (N / 8), r1 = (2 * t + 1) * (N / 8);
-    const int h0 = LI::hcol(rg) ^ LI::hcol(r0), p0 = LI::hrow(rg) ^ LI::hrow(r0);
-    const int h1 = LI::hcol(rg) ^ LI::hcol(r1), p1 = LI::hrow(rg) ^ LI::hrow(r1);
-    const int wr0 = 16 * t + 64 * g, wr1 = 16 * t + 8 + 64 * g;
-    const int wh0 = LO::hcol(16 * t) ^ LO::hcol(64 * g), wp0 = LO::hrow(16 * t) ^ LO::hrow(64 * g);
-    const int wh1 = LO::hcol(16 * t + 8) ^ LO::hcol(64 * g), wp1 = LO::hrow(16 * t + 8) ^ LO::hrow(64 * g);
-    float d[GROUPS][4];
-#pragma unroll
-    for (int G = 0; G < GROUPS; ++G) {
-        const int grp = w * GROUPS + G;
-        const int c = grp % CX, B0 = grp / CX, alpha = B0 & 7;
-        const int hb = LI::hcol(B0), pb = LI::hrow(B0);
-        float2 x0 = buf[LI::at(B0 + rg + r0, c, hb ^ h0, pb ^ p0)];
-        float2 x1 = buf[LI::at(B0 + rg + r1, c, hb ^ h1, pb ^ p1)];
-        // stage a: input m of a butterfly with b % 8 = alpha times exp(DIR 2 pi i alpha m / 64)
-        x0 = cmul(x0, twiddle1024<DIR>(tw, alpha * (2 * t) * 16));
-        x1 = cmul(x1, twiddle1024<DIR>(tw, alpha * (2 * t + 1) * 16));
-        const unsigned int cmb = PREC == 2 ? colmax[c] : 0u;   // one tile column per group
-        if (PREC == 2) {
-            const float sc = col_scale(cmb, false);
-            x0 = cscale(x0, sc);
-            x1 = cscale(x1, sc);
-        }
-        uint32_t bh0, bl0, bh1, bl1;
-        split2<PREC>(x0.x, x1.x, bh0, bl0);
-        split2<PREC>(x0.y, x1.y, bh1, bl1);
-        float e[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_16816<PREC>(e, al, bh0, bh1);
-        mma_16816<PREC>(e, ah, bl0, bl1);
-        mma_16816<PREC>(e, ah, bh0, bh1);
-        // stage b: butterfly 64 beta + 8 g + alpha, input r (= 2t, 2t + 1) times
-        // exp(DIR 2 pi i (8 g + alpha) r / 512)
-        const int kb = 8 * g + alpha;
-        const float2 y0 = cmul(make_float2(e[0], e[2]), twiddle1024<DIR>(tw, kb * (2 * t) * 2));
-        const float2 y1 = cmul(make_float2(e[1], e[3]), twiddle1024<DIR>(tw, kb * (2 * t + 1) * 2));
-        split2<PREC>(y0.x, y1.x, bh0, bl0);
-        split2<PREC>(y0.y, y1.y, bh1, bl1);
-        d[G][0] = d[G][1] = d[G][2] = d[G][3] = 0.f;
-        mma_16816<PREC>(d[G], al, bh0, bh1);
-        mma_16816<PREC>(d[G], ah, bl0, bl1);
-        mma_16816<PREC>(d[G], ah, bh0, bh1);
-        if (PREC == 2) {
-            const float us = col_scale(cmb, true);                // exact: a power of two
-#pragma unroll
-            for (int k = 0; k < 4; ++k) d[G][k] *= us;
-        }
-    }
-    __syncthreads();                                          // all inputs read
-#pragma unroll
-    for (int G = 0; G < GROUPS; ++G) {
-        const int grp = w * GROUPS + G;
-        const int c = grp % CX, B0 = grp / CX;
-        const int rb = 512 * (B0 >> 3) + (B0 & 7);
-        const int hb = LO::hcol(rb), pb = LO::hrow(rb);
-        buf[LO::at(rb + wr0, c, hb ^ wh0, pb ^ wp0)] = make_float2(d[G][0], d[G][2]);
-        buf[LO::at(rb + wr1, c, hb ^ wh1, pb ^ wp1)] = make_float2(d[G][1], d[G][3]);
-    }
-    __syncthreads();
-}
-
 // Radix-8 tensor-core stages while they fit, then one float32 stage of the rest.
 template <int LOGN, int CX, int DIR, int THREADS, int PREC, int NS>
 struct TcChain {
@@ -419,13 +317,14 @@ __device__ __forceinline__ void tc_colmax_deposit(float m, TcColMax& cmx) {
 }
 
 // In-place unnormalised DFT of every column of the tile (natural order in and
-// out; the input in the plain layout, the result in layout TcResult).
+// out; plain layout in and out).
 // Starts and ends with the tile fully written (callers synchronise before).
 // cmx: the column maxima of the float16-split form (PREC 2).  SCAN: the
 // transform reads the tile for them; otherwise every thread has already
 // deposited them (tc_colmax_deposit) before the caller's barrier.
 template <int LOGN, int CX, int DIR, int THREADS, int PREC, bool SCAN = true>
 __device__ __forceinline__ void tile_fft_tc(float2* buf, const float2* __restrict__ tw, TcColMax& cmx) {
+    static_assert(LOGN <= 5, "16- and 32-point lines (longer lines: tile_fft_tc5)");
     uint32_t ah[4], al[4];
     dft8_matrix<DIR, PREC>(threadIdx.x & 31, ah, al);
     unsigned int* colmax = cmx.m + 16 * cmx.cur;
@@ -444,20 +343,7 @@ __device__ __forceinline__ void tile_fft_tc(float2* buf, const float2* __restric
         __syncthreads();
     }
     cmx.cur ^= 1;
-    if constexpr (LOGN == 9 || LOGN == 10) {
-        // stride 1, then strides 8 and 64 in one pass, then (1024) a float32 radix-2 stage
-        constexpr int N = 1 << LOGN;
-        tc_stage8<N, CX, 1, DIR, THREADS, PREC, TcPlain<CX>, TcMid<LOGN, CX>>(buf, ah, al, tw, colmax);
-        tc_stage8x8<N, CX, DIR, THREADS, PREC, TcMid<LOGN, CX>, TcOut<CX>>(buf, ah, al, tw, colmax);
-        if constexpr (LOGN == 10) f32_stage<N, CX, 2, 512, DIR, THREADS, TcOut<CX>>(buf, tw);
-    } else {
-        TcChain<LOGN, CX, DIR, THREADS, PREC, 1>::run(buf, ah, al, tw, colmax);
-    }
+    TcChain<LOGN, CX, DIR, THREADS, PREC, 1>::run(buf, ah, al, tw, colmax);
 }
-
-// Layout of the tile that tile_fft_tc leaves: TcOut for 512-point lines (the
-// fused pass is the last), plain otherwise.
-template <int LOGN, int CX>
-using TcResult = std::conditional_t<LOGN == 9, TcOut<CX>, TcPlain<CX>>;
 
 }  // namespace kwgb

@@ -156,7 +156,7 @@ __device__ __forceinline__ void inverse_tile(float2 (&v)[E], int j, TileSmem<CX,
         } else {
             tile_fft_tc<LOGN, CX, +1, THREADS, MIXED, false>(tile, tw, cmx);
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = tile[TcResult<LOGN, CX>::idx(j + TL * m, S.c)];
+            for (int m = 0; m < E; ++m) v[m] = tile[(j + TL * m) * CX + S.c];
         }
     }
 }
@@ -282,7 +282,7 @@ yz_kernel(const __grid_constant__ YZK a) {
         } else if constexpr (MIXED != 0) {
             tile_fft_tc<LOGN, CX, (ISY ? (OP == OP_Y_FWD ? -1 : +1) : -1), THREADS, MIXED>(smem + s * STAGE, g.t.tw, cmx);
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = smem[s * STAGE + TcResult<LOGN, CX>::idx(j + TL * m, c)];
+            for (int m = 0; m < E; ++m) v[m] = smem[s * STAGE + (j + TL * m) * CX + c];
         } else {
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = S.raw(j + TL * m);
