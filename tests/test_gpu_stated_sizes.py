@@ -23,8 +23,9 @@ rel L2 bound (a necessary condition over every point).
   against 1.8 MPa at the bowl), so its outputs (p_max, p_rms, intensity)
   are compared on the scale of the same output over the plane sensor, which
   crosses the source (intensity: on the scale max|p| max|u_z| of the
-  fields): max |g - o| within 1e-4 of that scale, the accuracy of a float32
-  field after a few hundred FFT passes.
+  fields): max |g - o| within 1e-5 of that scale (float32 fields carry
+  about 1e-6 of their scale after the step's FFT passes; measured at most
+  5.6e-7 over the three forms).
 """
 
 import os
@@ -53,12 +54,13 @@ def _golden(name):
     return np.load(os.path.join(GOLDEN, name + ".npz"))
 
 
-def _sampled(got_full, d, key, idx_key, tl2, tinf):
+def _sampled(got_full, d, key, idx_key, tl2, tinf, form="f32"):
     """Errors of a full GPU output against the oracle's sampled values."""
     idx = d[idx_key].astype(np.int64)
     o = d[key].astype(np.float64)
     g = np.asarray(got_full, dtype=np.float64)
     e2, ei = rel_l2(g[..., idx], o), linf(g[..., idx], o)
+    print("ERRTABLE form=%s config=3 output=%s rel_l2=%.3e linf=%.3e" % (form, key, e2, ei))
     assert e2 <= tl2 and ei <= tinf, (key, e2, ei)
     norm = float(d[key + "_l2"])
     assert abs(np.linalg.norm(g) - norm) <= tl2 * norm, (key, np.linalg.norm(g), norm)
@@ -87,26 +89,32 @@ def test_segmented_bowl_128_forward_and_adjoint(kw):
     assert rel_l2(G, Go) <= 2e-3, rel_l2(G, Go)
 
 
-def test_hifu_512_first_steps(kw):
+@pytest.mark.parametrize("form,flag", [("f32", 0), ("f16", 8), ("bf16", 4)])
+def test_hifu_512_first_steps(kw, form, flag):
+    """The float32 form and both split-precision tensor-core forms against the
+    same oracle run (errors printed with -s)."""
     d = _golden("config3_512")
     steps = int(d["steps"])
     cfg = inputs.make_config(3, n_steps=steps + 4)
+    cfg["flags"] = cfg["flags"] | flag
     sim, ids = kw.from_config(cfg)
     sim.step(steps)
     focal, plane = ids
     for which, tag in ((P_MAX, "p_max"), (P_RMS, "p_rms")):
-        _sampled(sim.read(plane, which), d, "plane_" + tag, "plane_%s_idx" % tag, 1e-3, 5e-3)
+        _sampled(sim.read(plane, which), d, "plane_" + tag, "plane_%s_idx" % tag, 1e-3, 5e-3, form)
         g = sim.read(focal, which)
         idx = d["focal_%s_idx" % tag].astype(np.int64)
         scale = float(d["plane_%s_absmax" % tag])
         err = np.abs(g[idx] - d["focal_" + tag]).max() / scale
-        assert err <= 1e-4, (tag, err)
+        print("ERRTABLE form=%s config=3 output=focal_%s max_err/scale=%.3e" % (form, tag, err))
+        assert err <= 1e-5, (tag, err)
     # intensity p u: on the scale max|p| max|u_z| of the fields
     gi = sim.read(focal, I_AVG)
     idx = d["focal_I_idx"].astype(np.int64)
     scale = float(d["field_p_absmax"]) * float(d["field_uz_absmax"])
     err = np.abs(gi[:, idx] - d["focal_I"]).max() / scale
-    assert err <= 1e-4, err
+    print("ERRTABLE form=%s config=3 output=focal_I max_err/scale=%.3e" % (form, err))
+    assert err <= 1e-5, err
     for name in ("p", "uz", "rhoz"):
-        _sampled(sim.read_field(name).reshape(-1), d, "field_" + name, "field_%s_idx" % name, 1e-3, 5e-3)
+        _sampled(sim.read_field(name).reshape(-1), d, "field_" + name, "field_%s_idx" % name, 1e-3, 5e-3, form)
     sim.close()
