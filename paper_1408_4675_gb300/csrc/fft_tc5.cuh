@@ -226,6 +226,14 @@ __device__ __forceinline__ void tile_fft_tc5(float2* buf, Tc5& t, const float2* 
     const int m = 16 * q + (lane & 15);                // accumulator row of this lane
     const int k2 = m >> 1, ri = m & 1;
     const uint32_t lane_addr = t.tmem + ((uint32_t)(32 * q) << 16);
+    // the twiddles (global loads) are issued before the tensor-memory reads and
+    // their wait, so the two latencies overlap
+    float2 wts[NCW / 16];
+#pragma unroll
+    for (int u = 0; u < NCW / 16; ++u) {
+        const int a = (wg * NCW + 16 * u + 8 * (lane >> 4) + 4 * ri) / CX;
+        wts[u] = twiddle1024<-1>(tw, (a * k2 * (1024 / N)) & 1023);
+    }
     uint32_t rv[NCW / 16][8];
     if (t.ok) {
 #pragma unroll
@@ -245,7 +253,7 @@ __device__ __forceinline__ void tile_fft_tc5(float2* buf, Tc5& t, const float2* 
         // this lane finishes columns col0 .. col0 + 3 (even lane: the first four)
         const int col0 = wg * NCW + 16 * u + 8 * (lane >> 4) + 4 * ri;
         const int a = col0 / CX, c0 = col0 % CX;
-        const float2 wt = twiddle1024<-1>(tw, (a * k2 * (1024 / N)) & 1023);
+        const float2 wt = wts[u];
         const int ob = tc5_koff((k2 % N1) * CX + c0, 2 * N1 * (k2 / N1) + 2 * a);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
