@@ -437,16 +437,18 @@ def _homogeneous(cfg):
 
 def adjoint_measure(kwgb, torch):
     """Forward + hand-written adjoint of the 256-element segmented bowl at 128^3
-    (600 steps, checkpoint every 50): time per step of each leg and device
-    memory, beside the plain forward step of the same problem and the
-    objective-only run (one forward run, no checkpoints)."""
+    (600 steps), two ways: checkpoints every 50 steps (the reverse pass
+    recomputes each segment) and every step's density fields kept by the
+    forward run (7 fields a step, 35 GB; nothing recomputed).  Time per step of
+    each leg and device memory, beside the plain forward step of the same
+    problem and the objective-only run (one forward run, no checkpoints)."""
     from paper_1408_4675_gb300.autograd import FocalProblem
     cfg = inputs.make_config(5)
-    prob = FocalProblem(cfg, checkpoint_every=50)
-    nt = prob.n_steps
+    nt = int(cfg["n_steps"])
 
     def per_step(t0):
         return (time.perf_counter() - t0) * 1e3 / nt
+    prob = FocalProblem(cfg, checkpoint_every=50)
     warm = prob.simulation(cfg["phases"], cfg["amps"])     # one-time set-up (kernel attributes, graph capture)
     warm.step(8)
     warm.close()
@@ -461,19 +463,22 @@ def adjoint_measure(kwgb, torch):
     t0 = time.perf_counter()
     prob.objective(cfg["phases"], cfg["amps"])
     obj = per_step(t0)
-    t0 = time.perf_counter()
-    J, sim = prob.forward(cfg["phases"], cfg["amps"])
-    fwd_ck = per_step(t0)
-    t1 = time.perf_counter()
-    dphi, damp, _ = prob.backward(sim, cfg["phases"], cfg["amps"])
-    bwd = per_step(t1)
-    tot = per_step(t0)
-    return {"workload": "segmented_bowl_256_elements_128^3", "steps": nt, "checkpoint_every": 50,
-            "forward_ms_per_step": round(fwd, 4), "objective_only_ms_per_step": round(obj, 4),
-            "forward_with_checkpoints_ms_per_step": round(fwd_ck, 4), "reverse_ms_per_step": round(bwd, 4),
-            "forward_plus_adjoint_ms_per_step": round(tot, 4), "ratio_to_forward": round(tot / fwd, 3),
-            "device_gb": round(prob.last_device_bytes / 1e9, 3), "J": J,
-            "grad_norm_phases": float(np.linalg.norm(dphi))}
+    out = {"workload": "segmented_bowl_256_elements_128^3", "steps": nt,
+           "forward_ms_per_step": round(fwd, 4), "objective_only_ms_per_step": round(obj, 4)}
+    for name, K in (("checkpoint_every_50", 50), ("every_step_kept", nt)):
+        prob = FocalProblem(cfg, checkpoint_every=K)
+        t0 = time.perf_counter()
+        J, sim = prob.forward(cfg["phases"], cfg["amps"])
+        fwd_ck = per_step(t0)
+        t1 = time.perf_counter()
+        dphi, damp, _ = prob.backward(sim, cfg["phases"], cfg["amps"])
+        bwd = per_step(t1)
+        tot = per_step(t0)
+        out[name] = {"checkpoint_every": K, "forward_ms_per_step": round(fwd_ck, 4),
+                     "reverse_ms_per_step": round(bwd, 4), "forward_plus_adjoint_ms_per_step": round(tot, 4),
+                     "ratio_to_forward": round(tot / fwd, 3), "device_gb": round(prob.last_device_bytes / 1e9, 3),
+                     "J": J, "grad_norm_phases": float(np.linalg.norm(dphi))}
+    return out
 
 
 class CufftStep:

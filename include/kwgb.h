@@ -292,8 +292,14 @@ int kwgb_gradient_static_debug_wait_fault(int on);
  *   obj_idx    n_obj unique linear indices (host) of the objective region
  *   objective  KWGB_OBJ_MEAN_ABS_P (d|p|/dp taken as sign(p))
  *   n_steps    steps of the run (the simulation must not have stepped yet)
- *   checkpoint_every  K > 0: keep the state every K steps (device memory
- *              ~ (n_steps/K) * 7 fields) for kwgb_adjoint_backward;
+ *   checkpoint_every  0 < K < n_steps: keep the state every K steps
+ *              (device memory ~ (n_steps/K) * 7 fields) for
+ *              kwgb_adjoint_backward, which recomputes the steps between;
+ *              K >= n_steps: keep every step's density fields instead
+ *              (rho_xi, the Eq. 4c derivatives d_xi and the total density:
+ *              7 fields, 28 N bytes a step), written by the forward steps
+ *              themselves, so that the backward pass recomputes nothing
+ *              (OOM if they do not fit: take a smaller K);
  *              K = 0: the objective only (no checkpoints, no gradient later)
  *   J_out      objective value (host)
  * The simulation then holds the end state (n_steps taken) and its sensors
@@ -304,9 +310,11 @@ int kwgb_adjoint_forward(kwgb_sim* sim, const int64_t* obj_idx, int64_t n_obj, i
                          int64_t n_steps, int64_t checkpoint_every, double* J_out, void* cuda_stream);
 
 /* kwgb_adjoint_backward: the reverse pass of the run kwgb_adjoint_forward
- * made (checkpoint_every > 0).  Each K-step segment is recomputed from its
- * checkpoint, keeping rho_xi and the Eq. 4c derivatives d_xi of every step
- * (device memory ~ 6 K fields), then stepped backwards.
+ * made (checkpoint_every > 0).  With checkpoints, each K-step segment is
+ * recomputed from its checkpoint, keeping rho_xi, the Eq. 4c derivatives
+ * d_xi and the total density of every step (device memory ~ 7 K fields),
+ * then stepped backwards; with every step kept, the steps are stepped
+ * backwards directly.
  *   grad_out   host, grad_len doubles: for every source in add order, its
  *              n_signals rows of n_t values dJ/dsignal[row][n]
  * Afterwards the simulation holds the forward end state and sensor outputs

@@ -109,9 +109,14 @@ struct kwgb_sim {
     int64_t launches = 0;       // kernels launched so far
     bool adjoint_done = false;
     // adjoint: kwgb_adjoint_forward keeps what kwgb_adjoint_backward needs
-    float* adj_dout[3] = {nullptr, nullptr, nullptr};   // x_dens writes d_xi here when set (recomputation)
+    // x_dens keeps rho_xi^n, d_xi and rho^{n+1} of step n at
+    // adj_keep + (n mod adj_period) 7 N when set (XDensArgs::keep)
+    float* adj_keep = nullptr;
+    int64_t adj_period = 0;
     struct AdjRun {
         bool pending = false;            // forward with checkpoints done, reverse pass not yet run
+        bool keep_all = false;           // K >= n_steps: the forward run kept every step's fields
+        float* seg = nullptr;            // kept fields (keep_all: of every step, written by the forward run)
         int64_t n_steps = 0, K = 0, n_obj = 0;
         double w = 0.0;                  // 1 / (n_obj n_steps)
         char* ck = nullptr;              // checkpoints (u, rho_xi, P) every K steps
@@ -530,7 +535,12 @@ static int launch_step(kwgb_sim* sim, cudaStream_t s) {
     LKM(ypass(sim, +1, sp, sp, 3, s), K_Y_INV_DIV);
     // Eq. 4d + source; lossless: Eq. 6 + sensors + R2C of p here
     XDensArgs da{};
-    for (int a = 0; a < 3; ++a) { da.D[a] = sp[a]; da.rho[a] = sim->rho[a]; da.dout[a] = sim->adj_dout[a]; }
+    for (int a = 0; a < 3; ++a) {
+        da.D[a] = sp[a];
+        da.rho[a] = sim->rho[a];
+    }
+    da.keep = sim->adj_keep;
+    da.keep_period = sim->adj_period;
     const SensorC sens = sensor_c(sim);
     if (sim->md.absorbing) {
         da.S = sim->P;
@@ -1269,31 +1279,57 @@ extern "C" int kwgb_adjoint_forward(kwgb_sim* sim, const int64_t* obj_idx, int64
     sim->last_stream = s;
     auto& A = sim->adj;
     const int64_t K = checkpoint_every;
-    // objective points become an internal sensor (p of every step is read from its slots)
+    // the objective points become an internal p-series sensor of n_steps samples:
+    // the step itself (its series kernel, inside the captured step) records
+    // p^{n+1} at the points as sample n, laid out [n][point]
     int32_t osid = -1;
-    if (int e = kwgb_add_sensor(sim, obj_idx, n_obj, KWGB_P_MAX, &osid)) return e;
+    if (int e = kwgb_add_sensor(sim, obj_idx, n_obj, KWGB_P_SERIES, &osid)) return e;
+    if (int e = kwgb_set_series_capacity(sim, osid, n_steps)) return e;
     if (int e = freeze(sim)) return e;
     sim->adjoint_done = true;
-    const int64_t slot0 = sim->hsens[osid].slot0;
-    A.pobj = static_cast<float*>(dalloc(sim, (size_t)n_steps * n_obj * sizeof(float)));
-    if (!A.pobj) return fail(sim, KWGB_ERR_OOM, "adjoint objective samples");
-    if (K > 0) {
+    A.pobj = sim->sens.series + sim->hsens[osid].pser0;
+    const size_t F = (size_t)sim->N * sizeof(float);
+    A.keep_all = K >= n_steps;
+    if (A.keep_all) {
+        if (sim->gexec) {                      // a captured step without the kept fields
+            cudaGraphExecDestroy(sim->gexec);
+            sim->gexec = nullptr;
+        }
+        // every step's fields (7 N floats a step) instead of checkpoints: the
+        // reverse pass recomputes nothing
+        A.seg = static_cast<float*>(dalloc(sim, (size_t)n_steps * 7 * F));
+        if (!A.seg)
+            return fail(sim, KWGB_ERR_OOM, "keeping every step's fields for the adjoint (28 N bytes a step); "
+                                           "give a checkpoint interval below the step count");
+        sim->adj_keep = A.seg;
+        sim->adj_period = n_steps;
+    } else if (K > 0) {
         const int64_t nck = (n_steps + K - 1) / K;
         A.ck = static_cast<char*>(dalloc(sim, (size_t)nck * ck_bytes(sim)));
         A.fin = static_cast<char*>(dalloc(sim, ck_bytes(sim)));
         if (!A.ck || !A.fin) return fail(sim, KWGB_ERR_OOM, "adjoint checkpoints");
+    }
+    if (K > 0) {
         std::vector<int64_t> ov(obj_idx, obj_idx + n_obj);
         if (int e = upload(sim, &A.d_obj, ov)) return e;
     }
-    // ---- forward run, a checkpoint every K steps
+    // ---- forward run, a checkpoint every K steps (or every step's fields kept)
     for (int64_t n = 0; n < n_steps; ++n) {
-        if (K > 0 && n % K == 0)
+        if (K > 0 && !A.keep_all && n % K == 0)
             if (int e = save_ck(sim, A.ck + (size_t)(n / K) * ck_bytes(sim), s)) return e;
         if (int e = run_step(sim, s)) return e;
         sim->steps++;
-        if (int e = copy_dev(sim, A.pobj + n * n_obj, sim->sens.p_sens + slot0, n_obj * sizeof(float), s)) return e;
     }
-    if (K > 0) {
+    if (A.keep_all) {
+        // later steps keep nothing: drop the captured step that writes the fields
+        sim->adj_keep = nullptr;
+        sim->adj_period = 0;
+        if (sim->gexec) {
+            cudaGraphExecDestroy(sim->gexec);
+            sim->gexec = nullptr;
+        }
+    }
+    if (K > 0 && !A.keep_all) {
         if (int e = save_ck(sim, A.fin, s)) return e;
         // sensor accumulators as the forward run left them (the recomputation steps again)
         const SensorC& sc_ = sim->sens;
@@ -1357,10 +1393,13 @@ extern "C" int kwgb_adjoint_backward(kwgb_sim* sim, double* grad_out, int64_t gr
     const size_t N = (size_t)sim->N;
     const size_t F = N * sizeof(float);
     const int64_t n_steps = A.n_steps, K = A.K, n_obj = A.n_obj;
-    const int64_t nck = (n_steps + K - 1) / K;
-    const int64_t segK = std::min(K, n_steps);
-    // segment buffers: rho_xi^n (segK + 1 states) and d_xi (segK steps); adjoint fields
-    float* seg = static_cast<float*>(dalloc(sim, (size_t)(2 * segK + 1) * 3 * F));
+    const bool keep_all = A.keep_all;
+    // steps per segment: a checkpoint interval, or (every step kept) a graph's worth of reverse steps
+    const int64_t L = keep_all ? std::min<int64_t>(n_steps, 64) : K;
+    const int64_t nseg = (n_steps + L - 1) / L;
+    // kept fields, per step: rho_xi^n, d_xi, rho^{n+1} (of every step, or of one
+    // segment's steps, recomputed); adjoint fields
+    float* seg = keep_all ? A.seg : static_cast<float*>(dalloc(sim, (size_t)std::min(K, n_steps) * 7 * F));
     float* lam = static_cast<float*>(dalloc(sim, 8 * F));
     double* grad = static_cast<double*>(dalloc(sim, (size_t)std::max<int64_t>(rows, 1) * max_nt * sizeof(double)));
     if (!seg || !lam || !grad) return fail(sim, KWGB_ERR_OOM, "adjoint buffers");
@@ -1395,42 +1434,36 @@ extern "C" int kwgb_adjoint_backward(kwgb_sim* sim, double* grad_out, int64_t gr
     CK(cudaMemsetAsync(grad, 0, (size_t)std::max<int64_t>(rows, 1) * max_nt * sizeof(double), s));
     const GridC& g = sim->g;
     const bool absorbing = sim->md.absorbing != 0;
-    auto seg_rho = [&](int64_t k, int a) { return seg + ((size_t)k * 3 + a) * N; };
-    auto seg_d = [&](int64_t k, int a) { return seg + ((size_t)(segK + 1 + k) * 3 + a) * N; };
     AdjX ax{};
+    ax.keep = seg;
+    ax.keep_period = keep_all ? n_steps : K;
     ax.lam_p = lam;
     for (int a = 0; a < 3; ++a) {
         ax.lam_u[a] = lam + (1 + a) * N;
         ax.lam_rho[a] = lam + (4 + a) * N;
     }
     ax.lam_src = lam + 7 * N;
+    ax.nrev = d_rev;
     float2* sp[3] = {sim->T1, sim->T2, sim->T3};
     for (int a = 0; a < 3; ++a) ax.sp[a] = sp[a];
     float2* ab[3] = {sim->T1, sim->T2, nullptr};
-    // One segment of len steps after its checkpoint is loaded (device step
-    // counter n0, reverse counter n0 + len - 1): recompute it, keeping rho_xi^n
-    // and the d_xi of every step, then step it backwards.  Every pointer
-    // depends only on the position in the segment, so a full segment can be
-    // captured once and replayed for the others.
+    // One segment of len steps (device reverse counter at its last step): with
+    // checkpoints, recompute it from its loaded checkpoint (device step counter
+    // at its first step), x_dens keeping every step's fields; then step it
+    // backwards.  The kernels index the kept fields by the device counters, so
+    // a full segment can be captured once and replayed for the others.
     auto segment = [&](cudaStream_t st, int64_t len) -> int {
-        for (int64_t k = 0; k < len; ++k) {
-            for (int a = 0; a < 3; ++a) {
-                if (int e = copy_dev(sim, seg_rho(k, a), sim->rho[a], F, st)) return e;
-                sim->adj_dout[a] = seg_d(k, a);
-            }
-            const int e = launch_step(sim, st);
-            for (int a = 0; a < 3; ++a) sim->adj_dout[a] = nullptr;
+        if (!keep_all) {
+            sim->adj_keep = seg;
+            sim->adj_period = K;
+            int e = KWGB_OK;
+            for (int64_t k = 0; k < len && !e; ++k) e = launch_step(sim, st);
+            sim->adj_keep = nullptr;
+            sim->adj_period = 0;
             if (e) return e;
         }
-        for (int a = 0; a < 3; ++a)
-            if (int e = copy_dev(sim, seg_rho(len, a), sim->rho[a], F, st)) return e;
         cudaStream_t s = st;                                                  // for LK
         for (int64_t k = len - 1; k >= 0; --k) {
-            for (int a = 0; a < 3; ++a) {
-                ax.rho_before[a] = seg_rho(k, a);
-                ax.rho_after[a] = seg_rho(k + 1, a);
-                ax.d[a] = seg_d(k, a);
-            }
             LK(launch_adj_obj(n_obj, A.d_obj, A.pobj, d_rev, A.w, ax.lam_p, s));
             if (absorbing) {                                                  // Eq. 8 backwards
                 LK(launch_adj_x_absprep(g, sim->md, ax, s));
@@ -1444,29 +1477,29 @@ extern "C" int kwgb_adjoint_backward(kwgb_sim* sim, double* grad_out, int64_t gr
             LK(zop(sim, Z_DIV_FWD, sp, sp, s));
             LK(ypass(sim, +1, sp, sp, 3, s));
             LK(launch_adj_x_vel(g, sim->md, ax, s));                         // Eq. 4b backwards
-            LK(ypass(sim, -1, sp, sp, 3, s));                                 // transpose of Eq. 4a
-            LK(zop(sim, Z_DIV, sp, sp, s));
-            LK(ypass(sim, +1, sp, sp, 3, s));
-            LK(launch_adj_x_p(g, sim->md, ax, s));
-            LK(launch_adj_retreat(d_rev, s));
+            LK(ypass(sim, -1, sp, sp, 3, s));                                 // transpose of Eq. 4a:
+            LK(zop(sim, Z_DIV_SUM, sp, sp, s));                               // the three terms summed
+            LK(ypass(sim, +1, sp, sp, 1, s));                                 // into sp[0]
+            LK(launch_adj_x_p(g, sim->md, ax, s));                           // (steps d_rev back)
         }
         return KWGB_OK;
     };
     cudaGraphExec_t seg_exec = nullptr;
     bool direct_done = false;                  // a full segment has run directly (one-time set-up done)
     int64_t seg_launches = 0;
-    for (int64_t c = nck - 1; c >= 0; --c) {
-        const int64_t n0 = c * K, n1 = std::min(n0 + K, n_steps);
-        if (int e = load_ck(sim, A.ck + (size_t)c * ck_bytes(sim), n0, s)) return e;
+    for (int64_t c = nseg - 1; c >= 0; --c) {
+        const int64_t n0 = c * L, n1 = std::min(n0 + L, n_steps);
+        if (!keep_all)
+            if (int e = load_ck(sim, A.ck + (size_t)c * ck_bytes(sim), n0, s)) return e;
         const int64_t nr = n1 - 1;
         CK(cudaMemcpyAsync(d_rev, &nr, sizeof(int64_t), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));          // the host value nr goes out of scope
-        if (n1 - n0 == K && direct_done && !seg_exec && sim->cap) {
+        if (n1 - n0 == L && direct_done && !seg_exec && sim->cap) {
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(sim->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
                 const int64_t l0 = sim->launches;
                 const std::string err = sim->err;
-                const int e = segment(sim->cap, K);
+                const int e = segment(sim->cap, L);
                 const cudaError_t ce = cudaStreamEndCapture(sim->cap, &graph);
                 seg_launches = sim->launches - l0;
                 sim->launches = l0;
@@ -1478,18 +1511,18 @@ extern "C" int kwgb_adjoint_backward(kwgb_sim* sim, double* grad_out, int64_t gr
             }
             cudaGetLastError();
         }
-        if (n1 - n0 == K && seg_exec) {
+        if (n1 - n0 == L && seg_exec) {
             CK(cudaGraphLaunch(seg_exec, s));
             sim->launches += seg_launches;
         } else {
             if (int e = segment(s, n1 - n0)) return e;
-            if (n1 - n0 == K) direct_done = true;
+            if (n1 - n0 == L) direct_done = true;
         }
     }
     if (seg_exec) cudaGraphExecDestroy(seg_exec);
-    // ---- put back the forward end state and the sensors
-    if (int e = load_ck(sim, A.fin, n_steps, s)) return e;
-    {
+    // ---- put back the forward end state and the sensors (the recomputation stepped them)
+    if (!keep_all) {
+        if (int e = load_ck(sim, A.fin, n_steps, s)) return e;
         size_t off = 0;
         for (auto& q : A.sarr) {
             if (int e = copy_dev(sim, q.first, A.snap + off, q.second, s)) return e;

@@ -30,8 +30,9 @@
 //                lambda_src, R2C of lambda_d_xi -> sp[xi]; then y, z (Eq. 4a
 //                op per component), y
 //   adj_x_vel    C2R of sp[xi] -> Eq. 4b backwards -> lambda_u, R2C of
-//                lambda_g_xi -> sp[xi]; then y, z (Eq. 4c op), y
-//   adj_x_p      C2R of sp[0..2], summed -> lambda_p
+//                lambda_g_xi -> sp[xi]; then y (3 spectra), z (Eq. 4c op on
+//                each, summed into sp[0]), y (1 spectrum)
+//   adj_x_p      C2R of sp[0] -> lambda_p; steps the reverse-step counter back
 // Every kernel reads a row's spectra before it writes that row's spectra, so
 // the spectra can be read and written in place.
 #include "x_rows.cuh"
@@ -90,6 +91,8 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) adj_x_dens_kerne
     typename Sh::Smem S = Sh::row_smem(smem, r);
     const size_t rb = (size_t)rr * g.nx;
     const bool nl = md.nonlinear;
+    const size_t NN = (size_t)g.nx * g.ny * g.nz;
+    const float* kp = K.a.keep + (size_t)(*K.a.nrev % K.a.keep_period) * 7 * NN;   // step n's kept fields
 
     float2 lrt[E], labs[E], r0[E];
 #pragma unroll
@@ -101,11 +104,7 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) adj_x_dens_kerne
         float2 w = make_float2(c.x * c.x, c.y * c.y);
         if (nl) {                                     // dp/drho = c0^2 (1 + (B/A) rho / rho0)
             const float2 ba = med2(md.bona, md.bona_s, i);
-            float2 rt = make_float2(0.f, 0.f);
-            if (valid) {
-#pragma unroll
-                for (int xi = 0; xi < 3; ++xi) rt = cadd(rt, ld2(K.a.rho_after[xi] + i));
-            }
+            const float2 rt = valid ? ld2(kp + 6 * NN + i) : make_float2(0.f, 0.f);
             w.x *= 1.0f + __fdividef(ba.x * rt.x, r0[m].x);
             w.y *= 1.0f + __fdividef(ba.y * rt.y, r0[m].y);
         }
@@ -134,13 +133,13 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) adj_x_dens_kerne
             const int x = 2 * (j + TL * m);
             const size_t i = rb + x;
             const float2 lr = valid ? ld2(lrho + i) : make_float2(0.f, 0.f);
-            const float2 d = valid ? ld2(pick3c(K.a.d, xi) + i) : make_float2(0.f, 0.f);
+            const float2 d = valid ? ld2(kp + (3 + xi) * NN + i) : make_float2(0.f, 0.f);
             const float2 f = xi == 0 ? ldg2(g.t.pml[0] + x) : (xi == 1 ? make_float2(fy, fy) : make_float2(fz, fz));
             const float2 lrp = cadd(lr, lrt[m]);
             src[m] = cadd(src[m], lrp);
             float2 nlr, ld;
             if (nl) {
-                const float2 rb_ = valid ? ld2(pick3c(K.a.rho_before, xi) + i) : make_float2(0.f, 0.f);
+                const float2 rb_ = valid ? ld2(kp + xi * NN + i) : make_float2(0.f, 0.f);
                 const float dx_ = __fdividef(1.0f, 1.0f + 2.0f * g.dt * d.x);
                 const float dy_ = __fdividef(1.0f, 1.0f + 2.0f * g.dt * d.y);
                 nlr = make_float2(lrp.x * f.x * f.x * dx_, lrp.y * f.y * f.y * dy_);
@@ -225,27 +224,23 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) adj_x_p_kernel(c
     const bool valid = row < g.ny * g.nz;
     const int rr = valid ? row : 0;
     typename Sh::Smem S = Sh::row_smem(smem, r);
-    float2 acc[E], v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) acc[m] = make_float2(0.f, 0.f);
-#pragma unroll 1
-    for (int xi = 0; xi < 3; ++xi) {
-        row_c2r<LOGM>(pick3w(K.a.sp, xi) + (size_t)rr * g.nhp, S, j, valid, g.t.tw, v);
-#pragma unroll
-        for (int m = 0; m < E; ++m) acc[m] = cadd(acc[m], v[m]);
-    }
+    float2 v[E];
+    row_c2r<LOGM>(K.a.sp[0] + (size_t)rr * g.nhp, S, j, valid, g.t.tw, v);
     if (valid) {
 #pragma unroll
         for (int m = 0; m < E; ++m)
-            st2(K.a.lam_p + (size_t)rr * g.nx + 2 * (j + TL * m), make_float2(-acc[m].x, -acc[m].y));
+            st2(K.a.lam_p + (size_t)rr * g.nx + 2 * (j + TL * m), make_float2(-v[m].x, -v[m].y));
     }
+    // the last kernel of a reverse step: its readers of the step index (the
+    // objective and the source gradient) have finished, so step it back here
+    if (K.a.nrev && blockIdx.x == 0 && threadIdx.x == 0) *K.a.nrev -= 1;
 }
 
 __device__ __forceinline__ float medv(const float* f, float s, int64_t i) { return f ? f[i] : s; }
 
 // The reverse step's index n is read from the device counter nrev (so that a
 // captured segment of reverse steps serves every segment), and lowered by
-// adj_retreat_kernel at the end of each reverse step.
+// adj_x_p_kernel at the end of each reverse step.
 __global__ void adj_obj_kernel(int64_t n_obj, const int64_t* __restrict__ idx, const float* __restrict__ pobj,
                                const int64_t* __restrict__ nrev, double weight, float* lam_p) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -255,22 +250,26 @@ __global__ void adj_obj_kernel(int64_t n_obj, const int64_t* __restrict__ idx, c
     lam_p[idx[k]] += (float)(weight * sgn);
 }
 
+// One warp per signal row: the lanes stride over the row's points and the
+// partial sums meet in a fixed butterfly, so the result does not depend on
+// scheduling (the gradient is bitwise reproducible).
 __global__ void adj_src_kernel(int rows, const int32_t* __restrict__ row_ptr, const int64_t* __restrict__ pts,
                                const float* __restrict__ scale, const int32_t* __restrict__ nt,
                                const float* __restrict__ lam_src, Medium md, double* grad, int64_t stride,
                                const int64_t* __restrict__ nrev) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (r >= rows) return;                                     // whole warps
     const int64_t n = *nrev;
-    if (r >= rows || n >= nt[r]) return;
+    if (n >= nt[r]) return;
     double acc = 0.0;
-    for (int k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+    for (int k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) {
         const int64_t L = pts[k];
         acc += (double)lam_src[L] * (double)scale[k] / (double)medv(md.c0, md.c0_s, L);   // dt 2 / (3 c0 dx)
     }
-    grad[r * stride + n] += acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) grad[r * stride + n] += acc;
 }
-
-__global__ void adj_retreat_kernel(int64_t* nrev) { *nrev -= 1; }
 
 cudaError_t launch_adj_x_absprep(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s) {
     AdjXK K{g, m, a};
@@ -329,12 +328,7 @@ cudaError_t launch_adj_src(int rows, const int32_t* row_ptr, const int64_t* pts,
                            const int32_t* nt, const float* lam_src, const Medium& m, double* grad,
                            int64_t stride, const int64_t* nrev, cudaStream_t s) {
     if (rows <= 0) return cudaSuccess;
-    adj_src_kernel<<<(rows + 127) / 128, 128, 0, s>>>(rows, row_ptr, pts, scale, nt, lam_src, m, grad, stride, nrev);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adj_retreat(int64_t* nrev, cudaStream_t s) {
-    adj_retreat_kernel<<<1, 1, 0, s>>>(nrev);
+    adj_src_kernel<<<(rows + 7) / 8, 256, 0, s>>>(rows, row_ptr, pts, scale, nt, lam_src, m, grad, stride, nrev);
     return cudaGetLastError();
 }
 

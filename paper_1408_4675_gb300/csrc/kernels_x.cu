@@ -21,7 +21,8 @@ struct XDensK {
 
 
 // DIRICHLET: the launch has Dirichlet pressure sources; DOUT: it also writes
-// the Eq. 4c derivatives d_xi (the adjoint's recomputation).  Separate
+// the Eq. 4c derivatives d_xi, the densities it read and the new total
+// density (the adjoint's recomputation).  Separate
 // instantiations, so that the common path carries no code for them.
 template <int LOGM, bool FUSED_EOS, bool DIRICHLET, bool DOUT>
 __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(const XDensK K) {
@@ -40,6 +41,9 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
     const int gw = blockIdx.x * TPB + team, nw = gridDim.x * TPB;
     const int mygroups = gw < ngroups ? (ngroups - 1 - gw) / nw + 1 : 0;
 
+    const size_t NN = (size_t)g.nx * g.ny * g.nz;
+    float* kp = nullptr;                               // this step's kept fields
+    if (DOUT) kp = K.a.keep + (size_t)(*K.st.step % K.a.keep_period) * 7 * NN;
     if (mygroups > 0) stage_rows<LOGM>(stage, K.a.D[0], gw * RPW, nrows, g.nhp, lane);
     cp_async_commit();
     for (int gi = 0; gi < mygroups; ++gi) {
@@ -92,7 +96,10 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
                 }
                 const float2 rn = make_float2(nx_, ny_);
                 if (valid) st2(rho_xi + rb + x, rn);
-                if (DOUT && valid) st2(pick3f(K.a.dout, xi) + rb + x, d[m]);
+                if (DOUT && valid) {
+                    st2(kp + (3 + xi) * NN + rb + x, d[m]);
+                    st2(kp + xi * NN + rb + x, ro);
+                }
                 rt[m] = cadd(rt[m], rn);
                 s[m] = make_float2(fmaf(r0[m].x, d[m].x, s[m].x), fmaf(r0[m].y, d[m].y, s[m].y));
             }
@@ -162,6 +169,10 @@ __global__ void __launch_bounds__(XTHREADS, XShape<LOGM>::MINB) x_dens_kernel(co
                     }
                 }
             }
+        }
+        if (DOUT && valid) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) st2(kp + 6 * NN + rb + 2 * (j + TL * m), rt[m]);
         }
         if (FUSED_EOS) {
             // Eq. 6 without absorption: p = c0^2 (rho + B/2A rho^2 / rho0)
@@ -373,7 +384,8 @@ cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src, c
     XDensK K{g, m, src, dsrc, sens, st, a};
     const bool fused = !m.absorbing;
     const bool dir = dsrc.row_ptr != nullptr;
-    const bool dout = a.dout[0] != nullptr;
+    const bool dout = a.keep != nullptr;
+    if (dout && a.keep_period <= 0) return cudaErrorInvalidValue;
     if (dout && dir) return cudaErrorInvalidValue;          // the adjoint takes no Dirichlet sources
     switch (g.lognx - 1) {
 #define CASE(L)                                                                                          \

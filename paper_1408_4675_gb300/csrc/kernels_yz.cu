@@ -103,7 +103,7 @@ cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, floa
         a.map[0] = in[0]->zmap;
         a.nloads = 1;
         a.load_comp[0] = 0;
-    } else if (kind == Z_DIV || kind == Z_DIV_FWD) {
+    } else if (kind == Z_DIV || kind == Z_DIV_FWD || kind == Z_DIV_SUM) {
         for (int i = 0; i < 3; ++i) {
             a.map[i] = in[i]->zmap;
             a.load_comp[i] = i;
@@ -125,6 +125,7 @@ cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, floa
         case Z_GRAD_BWD: return launch_op(OP_Z_GRAD_BWD, a, g.lognz, items, s);
         case Z_DIV: return launch_op(OP_Z_DIV, a, g.lognz, items, s);
         case Z_DIV_FWD: return launch_op(OP_Z_DIV_FWD, a, g.lognz, items, s);
+        case Z_DIV_SUM: return launch_op(OP_Z_DIV_SUM, a, g.lognz, items, s);
         case Z_ABS: return launch_op(OP_Z_ABS, a, g.lognz, items, s);
     }
     return cudaErrorInvalidValue;

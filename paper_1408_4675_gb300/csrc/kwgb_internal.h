@@ -116,11 +116,12 @@ struct StepC {
 cudaError_t launch_y_pass(const GridC& g, int dir, const SpecBuf* const* in, float2* const* out,
                           int ncomp, int* flag, cudaStream_t s);
 
-enum ZOpKind { Z_GRAD_FWD = 0, Z_GRAD_BWD = 1, Z_DIV = 2, Z_ABS = 3, Z_DIV_FWD = 4 };
+enum ZOpKind { Z_GRAD_FWD = 0, Z_GRAD_BWD = 1, Z_DIV = 2, Z_ABS = 3, Z_DIV_FWD = 4, Z_DIV_SUM = 5 };
 // z forward FFT -> operator -> z inverse FFT:
 //   Z_GRAD_*: in[0] -> out[xi] (NULL skips a component)
 //   Z_DIV:    in[xi] -> out[xi]  (Eq. 4c operator)
 //   Z_DIV_FWD: in[xi] -> out[xi] (Eq. 4a operator per component; adjoint pass)
+//   Z_DIV_SUM: in[0..2] -> out[0] = sum over xi of the Eq. 4c operator on in[xi] (adjoint pass)
 //   Z_ABS:    in[0] -> out[0] with k^{y-2}, in[1] -> out[1] with k^{y-1} (NULL skips)
 cudaError_t launch_z_op(const GridC& g, int kind, const SpecBuf* const* in, float2* const* out,
                         int* flag, cudaStream_t s);
@@ -144,7 +145,12 @@ struct XDensArgs {
     float2* R;                // x-R2C of rho         (absorbing only)
     float* rho_tot;           // rho as real rows of pitch 2*nhp (absorbing only)
     float2* P;                // non-absorbing: x-R2C of p (EOS fused here)
-    float* dout[3];           // optional (adjoint recomputation): d_xi = Eq. 4c derivative, pitch nx
+    // adjoint: with keep set, the step also writes, at keep + k 7 N (k = step
+    // index mod keep_period, N = nx ny nz, pitch nx): rho_xi^n as read
+    // (+ xi N), the Eq. 4c derivative d_xi (+ (3 + xi) N) and
+    // rho^{n+1} = sum rho_xi after the sources (+ 6 N)
+    float* keep;
+    int64_t keep_period;
 };
 cudaError_t launch_x_dens(const GridC& g, const Medium& m, const SourceC& src, const SourceC& dsrc,
                           const SensorC& sens, const StepC& st, const XDensArgs& a,
@@ -189,10 +195,12 @@ struct AdjX {
     float* lam_u[3];          // lambda of u^{n+1/2} -> of u^{n-1/2}
     float* lam_rho[3];        // lambda of rho_xi^{n+1} -> of rho_xi^n
     float* lam_src;           // sum_xi lambda of rho_xi^{n+1} (source gradient)
-    const float* rho_before[3];   // rho_xi^n
-    const float* rho_after[3];    // rho_xi^{n+1}
-    const float* d[3];        // d_xi of the step (Eq. 4c derivative, from the recomputation)
+    // the forward step's kept fields, laid out as XDensArgs::keep: rho_xi^n,
+    // d_xi (Eq. 4c derivative), rho^{n+1}; step n's at keep + (n mod keep_period) 7 N
+    const float* keep;
+    int64_t keep_period;
     float2* sp[3];            // spectra (x transformed), pitch nhp
+    int64_t* nrev;            // reverse-step counter n, lowered by adj_x_p
 };
 // absorbing: R2C of c0^2 tau lambda_p -> sp[0] and of -c0^2 eta lambda_p -> sp[1]
 cudaError_t launch_adj_x_absprep(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
@@ -201,7 +209,7 @@ cudaError_t launch_adj_x_absprep(const GridC& g, const Medium& m, const AdjX& a,
 cudaError_t launch_adj_x_dens(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
 // C2R of sp[xi] (Eq. 4a op of lambda_d) -> Eq. 4b backwards -> lambda_u -> R2C of lambda_g_xi -> sp[xi]
 cudaError_t launch_adj_x_vel(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
-// lambda_p = -(C2R sp[0] + C2R sp[1] + C2R sp[2])
+// lambda_p = -C2R sp[0] (sp[0]: the transpose of Eq. 4a, its three terms summed); then *nrev -= 1 (if nrev)
 cudaError_t launch_adj_x_p(const GridC& g, const Medium& m, const AdjX& a, cudaStream_t s);
 // lambda_p[idx_k] += weight * sign(p^{n+1}_k), n = *nrev, samples pobj[n * n_obj + k]
 cudaError_t launch_adj_obj(int64_t n_obj, const int64_t* idx, const float* pobj, const int64_t* nrev, double weight,
@@ -210,7 +218,5 @@ cudaError_t launch_adj_obj(int64_t n_obj, const int64_t* idx, const float* pobj,
 cudaError_t launch_adj_src(int rows, const int32_t* row_ptr, const int64_t* pts, const float* scale,
                            const int32_t* nt, const float* lam_src, const Medium& m, double* grad,
                            int64_t stride, const int64_t* nrev, cudaStream_t s);
-// *nrev -= 1
-cudaError_t launch_adj_retreat(int64_t* nrev, cudaStream_t s);
 
 }  // namespace kwgb

@@ -22,6 +22,7 @@ cudaError_t yz_dispatch_f16(const YZK& a, int op, int logn, int items, cudaStrea
         case OP_Z_DIV: return by_size<OP_Z_DIV>(a, logn, items, s);
         case OP_Z_ABS: return by_size<OP_Z_ABS>(a, logn, items, s);
         case OP_Z_DIV_FWD: return by_size<OP_Z_DIV_FWD>(a, logn, items, s);
+        case OP_Z_DIV_SUM: return by_size<OP_Z_DIV_SUM>(a, logn, items, s);
     }
     return cudaErrorInvalidValue;
 }

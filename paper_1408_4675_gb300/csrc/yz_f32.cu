@@ -8,8 +8,10 @@ namespace kwgb {
 
 template <int L, int OP>
 static cudaError_t launch_f32(const YZK& a, int items, cudaStream_t s) {
-    // (1024-point y passes and absorption pass: the one-column form measured faster)
-    if constexpr (L >= 8 && !(L == 10 && (OP == OP_Z_ABS || OP < 2))) return launch_pair<L, OP>(a, items, s);
+    // (1024-point y passes and absorption pass: the one-column form measured faster;
+    // the summing divergence pass of the adjoint exists in the one-column form only)
+    if constexpr (L >= 8 && !(L == 10 && (OP == OP_Z_ABS || OP < 2)) && OP != OP_Z_DIV_SUM)
+        return launch_pair<L, OP>(a, items, s);
     else return launch_t<L, OP, 0>(a, items, s);
 }
 
@@ -32,6 +34,7 @@ cudaError_t yz_dispatch_f32(const YZK& a, int op, int logn, int items, cudaStrea
         case OP_Z_DIV: return by_size<OP_Z_DIV>(a, logn, items, s);
         case OP_Z_ABS: return by_size<OP_Z_ABS>(a, logn, items, s);
         case OP_Z_DIV_FWD: return by_size<OP_Z_DIV_FWD>(a, logn, items, s);
+        case OP_Z_DIV_SUM: return by_size<OP_Z_DIV_SUM>(a, logn, items, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -30,7 +30,7 @@
 namespace kwgb {
 
 enum { OP_Y_FWD = 0, OP_Y_INV = 1, OP_Z_GRAD_FWD = 2, OP_Z_GRAD_BWD = 3, OP_Z_DIV = 4, OP_Z_ABS = 5,
-       OP_Z_DIV_FWD = 6 };
+       OP_Z_DIV_FWD = 6, OP_Z_DIV_SUM = 7 };
 
 // Column c of a tile in shared memory.  The TMA lands element e of every
 // column as row e (CX float2, dense): raw(e).  The float32 passes (PP)
@@ -194,7 +194,8 @@ yz_kernel(const __grid_constant__ YZK a) {
     const int items = nchunk * lines * (ISY ? a.ncomp : 1);
     // loads per tile: compile-time where the operator fixes it, so that values kept
     // for the loads of a tile are provably dead at the end of the tile
-    constexpr int LC = (ISY || OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) ? 1 : ((OP == OP_Z_DIV || OP == OP_Z_DIV_FWD) ? 3 : 0);
+    constexpr int LC = (ISY || OP == OP_Z_GRAD_FWD || OP == OP_Z_GRAD_BWD) ? 1
+                       : ((OP == OP_Z_DIV || OP == OP_Z_DIV_FWD || OP == OP_Z_DIV_SUM) ? 3 : 0);
     const int L = LC ? LC : a.nloads;
     const int my = items > (int)blockIdx.x ? (items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int Q = my * L;
@@ -257,6 +258,7 @@ yz_kernel(const __grid_constant__ YZK a) {
     if (tid == 0 && Q > 0) issue(0);
     float kap[E];
     float lg[E];
+    float2 acc[E];                                   // OP_Z_DIV_SUM: the sum over the tile's loads
 #pragma unroll
     for (int m = 0; m < E; ++m) { kap[m] = 0.f; lg[m] = 0.f; }
 
@@ -368,6 +370,26 @@ yz_kernel(const __grid_constant__ YZK a) {
                     float2* out = out_ptr(a, xi) + off;
 #pragma unroll
                     for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, v[m]);
+                }
+            } else if (OP == OP_Z_DIV_SUM) {
+                // sum over xi of the Eq. 4c operator on load xi, then one inverse transform
+                const int xi = l;
+                const float2 dx = col < g.nh ? __ldg(g.t.dfx + col) : make_float2(0.f, 0.f);
+                const float2 dy = __ldg(g.t.dfy + y);
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    float2 d = xi == 0 ? dx : (xi == 1 ? dy : __ldg(g.t.dfz + j + TL * m));
+                    d = make_float2(-d.x, d.y);                      // i k e^{-ikd/2}
+                    const float2 t = cscale(cmul(v[m], d), kap[m]);
+                    acc[m] = xi == 0 ? t : cadd(acc[m], t);
+                }
+                if (xi == 2) {
+                    inverse_tile<LOGN, E, CX, THREADS, MIXED>(acc, j, S, smem + s * STAGE, g.t.tw, cmx, t5);
+                    if (valid) {
+                        float2* out = a.out[0] + off;
+#pragma unroll
+                        for (int m = 0; m < E; ++m) __stcs(out + (size_t)(j + TL * m) * es, acc[m]);
+                    }
                 }
             } else {                                   // OP_Z_ABS
                 const int t = l == 0 ? a.load_comp[0] : a.load_comp[1];

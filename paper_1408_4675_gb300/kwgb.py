@@ -332,9 +332,11 @@ class Simulation:
         return J.value, out
 
     def adjoint_forward(self, obj_idx, n_steps, checkpoint_every=50, stream=None):
-        """Run n_steps forward and return J = mean |p| over obj_idx; with
-        checkpoint_every > 0 the simulation keeps the checkpoints that
-        adjoint_backward() needs, with 0 it computes J only."""
+        """Run n_steps forward and return J = mean |p| over obj_idx.  With
+        0 < checkpoint_every < n_steps the simulation keeps the checkpoints
+        that adjoint_backward() recomputes from; with checkpoint_every >=
+        n_steps it keeps every step's density fields (28 N bytes a step) and
+        adjoint_backward() recomputes nothing; with 0 it computes J only."""
         obj = np.ascontiguousarray(np.asarray(obj_idx, dtype=np.int64))
         J = ctypes.c_double()
         self._check(self.L.kwgb_adjoint_forward(self.h, _ptr(obj), obj.size, 0, int(n_steps), int(checkpoint_every),
