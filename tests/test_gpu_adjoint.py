@@ -1,7 +1,8 @@
 """GPU adjoint (kwgb_adjoint) against the FP64 oracle adjoint (lossless and
-absorbing media), checkpoint
-invariance, the autograd wrapper against central finite differences, and its
-forward-only and deferred-backward semantics.
+absorbing media; cubic grids and thin grids with 256- and 1024-point z
+lines), checkpoint invariance (including every step kept), the autograd
+wrapper against central finite differences, and its forward-only and
+deferred-backward semantics.
 
 Tolerances: objective J 1e-3 relative; per-sample gradients dJ/ds relative
 L2 2e-3 against the oracle adjoint; phase gradients 1e-2 against FP32
@@ -78,6 +79,49 @@ def test_adjoint_absorbing_matches_oracle(kw):
     assert abs(J - Jo) <= 1e-3 * abs(Jo), (J, Jo)
     G = np.stack([x[0] for x in g])
     Go = np.stack(go)
+    assert rel_l2(G, Go) <= 2e-3, rel_l2(G, Go)
+
+
+def _line_problem(nz, steps, absorbing):
+    """A thin grid (nz x 8 x 16) with long z lines: six elements of three
+    points on the plane just inside the z PML, a 3^3 focal box ten cells
+    beyond it, a smooth random c0 (and alpha0 when absorbing)."""
+    shape = (nz, 8, 16)
+    dx = 1e-4
+    zs = 21
+    c0 = inputs.smooth_random_field(shape, 1450.0, 1550.0, 71, 1.5)
+    c_ref = float(c0.max())
+    elems = [np.sort(inputs.linear_index(shape, [zs] * 3, [2 + e % 4] * 3, [3 + 2 * e, 4 + 2 * e, 5 + 2 * e]))
+             for e in range(6)]
+    rng = np.random.default_rng(72)
+    cfg = dict(shape=shape, d=(dx, dx, dx), dt=0.3 * dx / c_ref, c_ref=c_ref, flags=1 | (2 if absorbing else 0),
+               alpha_power=1.5, c0=c0, rho0=1000.0, bona=5.0,
+               alpha0=inputs.db_to_neper(inputs.smooth_random_field(shape, 0.5, 1.5, 73, 1.5), 1.5)
+               if absorbing else 0.0,
+               p0=None, elements=elems, phases=rng.uniform(-0.2, 0.2, 6), amps=np.full(6, 2e5), freq=1e6,
+               focal=inputs.box_mask(shape, (zs + 10, 4, 8), 1), n_steps=steps,
+               pml_size=(2, 1, 20), pml_alpha=(2.0, 2.0, 2.0))
+    cfg["sensors"] = [(cfg["focal"], 1)]
+    return cfg
+
+
+@pytest.mark.parametrize("nz,absorbing,k", [(256, False, 16), (1024, True, 40)])
+def test_adjoint_long_z_lines_matches_oracle(kw, nz, absorbing, k):
+    """The reverse step's z passes on 256- and 1024-point lines (the
+    two-columns-per-thread Eq. 4a operator pass and the summing Eq. 4c pass;
+    at 1024 points the absorption pass as well), with checkpoints every 16
+    steps and with every step kept (k = 40 = the step count), against the
+    oracle adjoint."""
+    from paper_1408_4675_gb300.autograd import FocalProblem
+    steps = 40
+    cfg = _line_problem(nz, steps, absorbing)
+    prob = FocalProblem(cfg, n_steps=steps, checkpoint_every=k)
+    J, dphi, damp, g = prob.value_and_grad(cfg["phases"], cfg["amps"])
+    Jo, go = _oracle_grads(cfg, steps)
+    assert J > 0 and abs(J - Jo) <= 1e-3 * abs(Jo), (J, Jo)
+    G = np.stack([x[0] for x in g])
+    Go = np.stack(go)
+    assert np.abs(Go).max() > 0
     assert rel_l2(G, Go) <= 2e-3, rel_l2(G, Go)
 
 
