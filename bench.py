@@ -16,7 +16,10 @@ algorithmic bytes per launch over its event-timed duration against the
 measured HBM copy bandwidth.
 
 ``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
-host cores instead, on a bounded sample of the same workload.
+host cores instead: W warm-up and K timed steps of the same workload.
+``--oracle-table`` times the oracle on every workload at its stated size
+beside the GPU step of the same workload (a CPU-baseline table, not the
+bench line).
 """
 
 import argparse
@@ -28,6 +31,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from types import SimpleNamespace
 
 import numpy as np
 
@@ -57,6 +61,9 @@ def parse():
     ap.add_argument("--profile-case", type=int, nargs=3, metavar=("NZ", "NY", "NX"), default=None,
                     help="small case for ncu captures: a heterogeneous nonlinear absorbing medium on an "
                          "NZ x NY x NX grid stepped --steps times, no timing")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="CPU-baseline table instead of the bench line: the FP64 oracle on every workload "
+                         "at its stated size on the host cores, beside the GPU step of the same workload")
     ap.add_argument("--profile-flags", type=int, default=0,
                     help="extra grid flags of the profiling case (4: bfloat16-split, 8: float16-split form)")
     return ap.parse_args()
@@ -104,7 +111,9 @@ class Replicas:
 
 def workload_name(cfg):
     n = cfg["shape"][0]
-    return "hifu_bowl_layered_tissue_%d^3" % n
+    kind = {1: "water_gaussian_initial_pressure", 2: "smooth_random_heterogeneous_tone_burst",
+            5: "segmented_bowl_256_elements"}.get(cfg.get("config"), "hifu_bowl_layered_tissue")
+    return "%s_%d^3" % (kind, n)
 
 
 # ---------------------------------------------------------------- byte model
@@ -704,8 +713,36 @@ def run_profile_case(args):
     sim.close()
 
 
+def run_oracle_table(args):
+    """The CPU-baseline leg over every workload at its stated size: the FP64
+    oracle on the host cores (one warm-up step, then configs 1 and 5 over
+    their whole runs of 200 and 600 steps, config 2 over 20 steps and config 3
+    over 5, each step timed), beside the GPU's event-timed step of the same
+    workload (5 warm-up + 50 steps).  Config 4 is not run: its FP64 oracle
+    state (about 480 GB at 1024^3) exceeds the host memory."""
+    import torch
+    from paper_1408_4675_gb300 import build, kwgb
+    build.build()
+    kwgb.load()
+    rows = []
+    for cid, steps in ((1, 200), (5, 600), (2, 20), (3, 5)):
+        sec, per, cores = oracle_timed(cid, None, 1, steps)
+        gpu = step_variant(SimpleNamespace(warmup=5, steps=50), kwgb, torch, cid, 0)
+        rows.append({"config": cid, "workload": gpu["workload"], "oracle_steps": steps,
+                     "oracle_ms_per_step": round(1e3 * sec, 2), "oracle_cores": cores,
+                     "gpu_ms_per_step": gpu["ms_per_step"],
+                     "oracle_over_gpu": round(1e3 * sec / gpu["ms_per_step"], 1)})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"oracle_table": rows,
+                      "not_run": {"config": 4, "why": "FP64 oracle state at 1024^3 (about 480 GB) exceeds the "
+                                                     "host memory"}}))
+
+
 def main():
     args = parse()
+    if args.oracle_table:
+        run_oracle_table(args)
+        return
     if args.profile_case is not None:
         run_profile_case(args)
         return
