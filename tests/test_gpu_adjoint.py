@@ -1,6 +1,7 @@
 """GPU adjoint (kwgb_adjoint) against the FP64 oracle adjoint (lossless and
 absorbing media; cubic grids and thin grids with 256- and 1024-point z
-lines), checkpoint invariance (including every step kept), the autograd
+lines; the float16- and bfloat16-split forms), checkpoint invariance
+(including every step kept), the autograd
 wrapper against central finite differences, and its forward-only and
 deferred-backward semantics.
 
@@ -82,11 +83,11 @@ def test_adjoint_absorbing_matches_oracle(kw):
     assert rel_l2(G, Go) <= 2e-3, rel_l2(G, Go)
 
 
-def _line_problem(nz, steps, absorbing):
-    """A thin grid (nz x 8 x 16) with long z lines: six elements of three
+def _line_problem(nz, steps, absorbing, ny=8):
+    """A thin grid (nz x ny x 16) with long z lines: six elements of three
     points on the plane just inside the z PML, a 3^3 focal box ten cells
     beyond it, a smooth random c0 (and alpha0 when absorbing)."""
-    shape = (nz, 8, 16)
+    shape = (nz, ny, 16)
     dx = 1e-4
     zs = 21
     c0 = inputs.smooth_random_field(shape, 1450.0, 1550.0, 71, 1.5)
@@ -123,6 +124,28 @@ def test_adjoint_long_z_lines_matches_oracle(kw, nz, absorbing, k):
     Go = np.stack(go)
     assert np.abs(Go).max() > 0
     assert rel_l2(G, Go) <= 2e-3, rel_l2(G, Go)
+
+
+@pytest.mark.parametrize("form,flag,tol", [("f32", 0, 2e-3), ("f16", 8, 2e-3), ("bf16", 4, 2e-3)])
+def test_adjoint_split_precision_forms_match_oracle(kw, form, flag, tol):
+    """The reverse step in the float16- and bfloat16-split tensor-core forms
+    beside float32: 64 x 64 x 16, absorbing, so that the y and z passes
+    (including the adjoint's own z passes) run on the tcgen05 form; the
+    focal box ten cells from the elements, 40 steps, so that the adjoint wave
+    reaches them; every step kept.  Against the oracle adjoint (prints the
+    errors with -s)."""
+    from paper_1408_4675_gb300.autograd import FocalProblem
+    steps = 40
+    cfg = _line_problem(64, steps, True, ny=64)
+    cfg["flags"] = cfg["flags"] | flag
+    prob = FocalProblem(cfg, n_steps=steps, checkpoint_every=steps)
+    J, dphi, damp, g = prob.value_and_grad(cfg["phases"], cfg["amps"])
+    Jo, go = _oracle_grads(cfg, steps)
+    G = np.stack([x[0] for x in g])
+    Go = np.stack(go)
+    print("ADJERR form=%s J_rel=%.3e grad_rel_l2=%.3e" % (form, abs(J - Jo) / abs(Jo), rel_l2(G, Go)))
+    assert abs(J - Jo) <= 1e-3 * abs(Jo), (J, Jo)
+    assert rel_l2(G, Go) <= tol, rel_l2(G, Go)
 
 
 def test_checkpoint_interval_does_not_change_the_gradient(kw):
