@@ -717,6 +717,39 @@ extern "C" int kwgb_set_series_capacity(kwgb_sim* sim, int32_t sensor_id, int64_
     return KWGB_OK;
 }
 
+// Stable sort of entries (member L, a linear index x + nx row) by L: a
+// counting sort by row, then a stable sort by x inside each row (insertion
+// sort for short rows, std::stable_sort for long unsorted ones).  The order
+// is that of std::stable_sort by L; the cost is O(n + rows) when the entries
+// of each row arrive in x order (masks built from boxes and planes).
+template <typename T>
+static void sort_by_index(std::vector<T>& v, int64_t nx, int64_t nrows) {
+    if (v.size() < 2) return;
+    std::vector<int64_t> begin(nrows + 1, 0);
+    for (const T& e : v) begin[e.L / nx + 1]++;
+    for (int64_t r = 0; r < nrows; ++r) begin[r + 1] += begin[r];
+    std::vector<int64_t> cur(begin.begin(), begin.end() - 1);
+    std::vector<T> out(v.size());
+    for (const T& e : v) out[cur[e.L / nx]++] = e;
+    auto lessL = [](const T& a, const T& b) { return a.L < b.L; };
+    for (int64_t r = 0; r < nrows; ++r) {
+        T* lo = out.data() + begin[r];
+        T* hi = out.data() + begin[r + 1];
+        if (hi - lo < 2 || std::is_sorted(lo, hi, lessL)) continue;
+        if (hi - lo > 32) {
+            std::stable_sort(lo, hi, lessL);
+            continue;
+        }
+        for (T* p = lo + 1; p < hi; ++p) {
+            const T e = *p;
+            T* k = p;
+            for (; k > lo && (k - 1)->L > e.L; --k) *k = *(k - 1);
+            *k = e;
+        }
+    }
+    v.swap(out);
+}
+
 // Row-CSR device lists of the sources of one kind (unique points per grid
 // row, each with its contributions: signal offset, length and scale sc).
 static int build_sources(kwgb_sim* sim, int mode, float sc, SourceC* out) {
@@ -726,6 +759,16 @@ static int build_sources(kwgb_sim* sim, int mode, float sc, SourceC* out) {
     struct Contrib { int64_t L; int64_t off; int32_t nt; };
     std::vector<Contrib> cs;
     std::vector<float> sig;
+    {
+        size_t nc = 0, ns = 0;
+        for (auto& s : sim->hsrc)
+            if (s.mode == mode) {
+                nc += s.idx.size();
+                ns += s.sig.size();
+            }
+        cs.reserve(nc);
+        sig.reserve(ns);
+    }
     for (auto& s : sim->hsrc) {
         if (s.mode != mode) continue;
         const int64_t base = (int64_t)sig.size();
@@ -734,7 +777,7 @@ static int build_sources(kwgb_sim* sim, int mode, float sc, SourceC* out) {
             cs.push_back({s.idx[i], base + (s.nsig == 1 ? 0 : (int64_t)i * s.nt), (int32_t)s.nt});
     }
     if (!cs.empty()) {
-        std::stable_sort(cs.begin(), cs.end(), [](const Contrib& a, const Contrib& b) { return a.L < b.L; });
+        sort_by_index(cs, nx, nrows);
         std::vector<int32_t> row_ptr(nrows + 1, 0), pt_x, pt_c;
         std::vector<int64_t> c_off;
         std::vector<int32_t> c_nt;
@@ -790,6 +833,17 @@ static int freeze(kwgb_sim* sim) {
     std::vector<int64_t> ii;
     std::vector<int32_t> islot;
     int64_t slots = 0;
+    {
+        int64_t ne = 0, ni = 0;
+        for (auto& h : sim->hsens)
+            if (!h.full) {
+                ne += h.n;
+                ni += (h.record & KWGB_I_AVG) ? h.n : 0;
+            }
+        es.reserve(ne);
+        ii.reserve(ni);
+        islot.reserve(ni);
+    }
     for (auto& h : sim->hsens) {
         if (h.full) {
             h.full_k = sc.nfull;
@@ -814,12 +868,12 @@ static int freeze(kwgb_sim* sim) {
     }
     sim->n_slots = slots;
     if (!es.empty()) {
-        std::stable_sort(es.begin(), es.end(), [](const Entry& a, const Entry& b) { return a.L < b.L; });
-        std::vector<int32_t> row_ptr(nrows + 1, 0), ex, eslot;
-        for (auto& e : es) {
-            row_ptr[e.L / nx + 1]++;
-            ex.push_back((int32_t)(e.L % nx));
-            eslot.push_back(e.slot);
+        sort_by_index(es, nx, nrows);
+        std::vector<int32_t> row_ptr(nrows + 1, 0), ex(es.size()), eslot(es.size());
+        for (size_t i = 0; i < es.size(); ++i) {
+            row_ptr[es[i].L / nx + 1]++;
+            ex[i] = (int32_t)(es[i].L % nx);
+            eslot[i] = es[i].slot;
         }
         for (int64_t r = 0; r < nrows; ++r) row_ptr[r + 1] += row_ptr[r];
         int32_t *d_rp, *d_ex, *d_es;
@@ -837,7 +891,7 @@ static int freeze(kwgb_sim* sim) {
         CK(cudaMemset(sc.p_sens, 0, slots * sizeof(float)));
         // p_min and the series rings (time-varying outputs at the sensor mask, Sec. 3.4)
         bool any_min = false, any_pser = false;
-        std::vector<SeriesSlot> ser(slots, SeriesSlot{-1, 0, 1});
+        std::vector<SeriesSlot> ser;                     // built when a sensor records the p series
         std::vector<int64_t> uidx;
         std::vector<SeriesSlot> uq;
         int64_t ptot = 0, utot = 0;
@@ -847,6 +901,7 @@ static int freeze(kwgb_sim* sim) {
             if ((h.record & (KWGB_P_SERIES | KWGB_U_SERIES)) && h.cap <= 0)
                 return fail(sim, KWGB_ERR_ARG, "a series sensor needs kwgb_set_series_capacity before stepping");
             if (h.record & KWGB_P_SERIES) {
+                if (!any_pser) ser.assign(slots, SeriesSlot{-1, 0, 1});
                 any_pser = true;
                 h.pser0 = ptot;
                 for (int64_t i = 0; i < h.n; ++i) ser[h.slot0 + i] = SeriesSlot{ptot + i, (int32_t)h.n, (int32_t)h.cap};
