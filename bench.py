@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--oracle-table", action="store_true",
                     help="CPU-baseline table instead of the bench line: the FP64 oracle on every workload "
                          "at its stated size on the host cores, beside the GPU step of the same workload")
+    ap.add_argument("--profile-adjoint", type=int, nargs=2, metavar=("N", "STEPS"), default=None,
+                    help="small case for ncu captures of the adjoint: the segmented bowl on an N^3 grid, "
+                         "STEPS forward steps keeping every step's fields, then the reverse pass; no timing")
     ap.add_argument("--profile-flags", type=int, default=0,
                     help="extra grid flags of the profiling case (4: bfloat16-split, 8: float16-split form)")
     return ap.parse_args()
@@ -738,8 +741,26 @@ def run_oracle_table(args):
                                                      "host memory"}}))
 
 
+def run_profile_adjoint(args):
+    """The adjoint of the segmented bowl (256 elements) on an N^3 grid for
+    `ncu` launch lists: one forward run of STEPS steps keeping every step's
+    fields, then the reverse pass."""
+    from paper_1408_4675_gb300 import build, kwgb
+    from paper_1408_4675_gb300.autograd import FocalProblem
+    build.build()
+    kwgb.load()
+    n, steps = args.profile_adjoint
+    cfg = inputs.make_config(5, n=n, n_steps=steps)
+    prob = FocalProblem(cfg, n_steps=steps, checkpoint_every=steps)
+    J, dphi, damp, _ = prob.value_and_grad(cfg["phases"], cfg["amps"])
+    print(json.dumps({"profile_adjoint": [n, steps], "J": J, "grad_norm_phases": float(np.linalg.norm(dphi))}))
+
+
 def main():
     args = parse()
+    if args.profile_adjoint is not None:
+        run_profile_adjoint(args)
+        return
     if args.oracle_table:
         run_oracle_table(args)
         return
