@@ -1369,21 +1369,26 @@ extern "C" int kwgb_adjoint_forward(kwgb_sim* sim, const int64_t* obj_idx, int64
         if (int e = upload(sim, &A.d_obj, ov)) return e;
     }
     // ---- forward run, a checkpoint every K steps (or every step's fields kept)
-    for (int64_t n = 0; n < n_steps; ++n) {
-        if (K > 0 && !A.keep_all && n % K == 0)
-            if (int e = save_ck(sim, A.ck + (size_t)(n / K) * ck_bytes(sim), s)) return e;
-        if (int e = run_step(sim, s)) return e;
-        sim->steps++;
-    }
-    if (A.keep_all) {
-        // later steps keep nothing: drop the captured step that writes the fields
+    auto stop_keeping = [&]() {               // later steps keep nothing: drop the step that writes the fields
+        if (!A.keep_all) return;
         sim->adj_keep = nullptr;
         sim->adj_period = 0;
         if (sim->gexec) {
             cudaGraphExecDestroy(sim->gexec);
             sim->gexec = nullptr;
         }
+    };
+    for (int64_t n = 0; n < n_steps; ++n) {
+        int e = KWGB_OK;
+        if (K > 0 && !A.keep_all && n % K == 0) e = save_ck(sim, A.ck + (size_t)(n / K) * ck_bytes(sim), s);
+        if (!e) e = run_step(sim, s);
+        if (e) {
+            stop_keeping();
+            return e;
+        }
+        sim->steps++;
     }
+    stop_keeping();
     if (K > 0 && !A.keep_all) {
         if (int e = save_ck(sim, A.fin, s)) return e;
         // sensor accumulators as the forward run left them (the recomputation steps again)
