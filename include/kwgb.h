@@ -49,7 +49,9 @@ extern "C" {
 /* ---- grid flags (kwgb_grid_desc.flags) ---------------------------------- */
 #define KWGB_NONLINEAR   1u  /* Eq. 4d denominator and (B/2A) rho^2/rho0 of Eq. 6 */
 #define KWGB_ABSORBING   2u  /* power-law absorption/dispersion L_d of Eq. 8     */
-#define KWGB_MIXED_BF16  4u  /* y/z FFT stages as bfloat16-split tensor-core products (radix 8, float32 accumulation); needs ny, nz >= 16 */
+#define KWGB_MIXED_BF16  4u  /* y/z FFTs as bfloat16-split tensor-core products with float32 accumulation
+                                (tcgen05 radix-32 stages for lines of 64 points and more, mma.sync radix-8
+                                for 16- and 32-point lines); needs ny, nz >= 16 */
 #define KWGB_MIXED_F16   8u  /* same with float16 hi + lo and a per-column power-of-two scale; needs ny, nz >= 16 */
 
 /* ---- sensor outputs (kwgb_add_sensor record / kwgb_read which) ---------- */
@@ -191,6 +193,9 @@ int kwgb_set_series_capacity(kwgb_sim* sim, int32_t sensor_id, int64_t n_t);
 /* Advance n_steps time steps, (u^{n-1/2}, rho^n, p^n) -> (u^{n+1/2},
  * rho^{n+1}, p^{n+1}) per step, asynchronously on cuda_stream (a
  * cudaStream_t; NULL = the legacy default stream).  n_steps == 0 is a no-op.
+ * The first call builds the device lists of the sources and sensors (the
+ * indices grouped by grid row on the host, uploaded, one device
+ * synchronisation); from then on sources and sensors are fixed.
  * The first step of a simulation launches its kernels directly and the
  * library then captures one step into a CUDA graph (on a stream of its own)
  * that later steps replay on cuda_stream; if capture is not possible the
