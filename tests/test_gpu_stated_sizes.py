@@ -18,17 +18,17 @@ rel L2 bound (a necessary condition over every point).
   focal objective J = mean |p| within 1e-3, focal p_max rel L2 within 1e-3,
   and the adjoint's dJ/ds of every element and sample within 2e-3 (rel L2)
   of the oracle's adjoint, checkpoints every 50 steps.
-* 512^3 HIFU workload, the first 12 steps (a 512^3 step of the FP64 oracle
+* 512^3 HIFU workload, the first 300 steps (a 512^3 step of the FP64 oracle
   takes about 12 s on 16 host cores, so the recipe's 3000 steps are out of
-  reach): the xz-plane sensor (p_max, p_rms) and the p, u_z, rho_z fields
-  within 1e-3 / 5e-3.  The focal box lies 64 mm from the bowl: after 12
-  steps it holds only the spectral precursor of the source (|p| of a few Pa
-  against 1.8 MPa at the bowl), so its outputs (p_max, p_rms, intensity)
-  are compared on the scale of the same output over the plane sensor, which
-  crosses the source (intensity: on the scale max|p| max|u_z| of the
-  fields): max |g - o| within 1e-5 of that scale (float32 fields carry
-  about 1e-6 of their scale after the step's FFT passes; measured at most
-  5.6e-7 over the three forms).
+  reach; 300 steps take an hour): the xz-plane sensor (p_max, p_rms) and the
+  p, u_z, rho_z fields within 1e-3 / 5e-3.  The focal box lies 64 mm (427
+  cells) from the bowl and the wave has travelled about 90 cells: the box
+  holds only the spectral precursor of the source, so its outputs (p_max,
+  p_rms, intensity) are compared on the scale of the same output over the
+  plane sensor, which crosses the source (intensity: on the scale
+  max|p| max|u_z| of the fields): max |g - o| within 1e-4 of that scale,
+  fifty times tighter than the workload's L-infinity row of 5e-3 (measured:
+  5.6e-7 float32, 1.4e-5 float16 split).
 """
 
 import os
@@ -107,7 +107,7 @@ def test_segmented_bowl_128_forward_and_adjoint(kw):
 
 
 @pytest.mark.parametrize("form,flag", [("f32", 0), ("f16", 8), ("bf16", 4)])
-def test_hifu_512_first_steps(kw, form, flag):
+def test_hifu_512_first_300_steps(kw, form, flag):
     """The float32 form and both split-precision tensor-core forms against the
     same oracle run (errors printed with -s)."""
     d = _golden("config3_512")
@@ -124,14 +124,14 @@ def test_hifu_512_first_steps(kw, form, flag):
         scale = float(d["plane_%s_absmax" % tag])
         err = np.abs(g[idx] - d["focal_" + tag]).max() / scale
         print("ERRTABLE form=%s config=3 output=focal_%s max_err/scale=%.3e" % (form, tag, err))
-        assert err <= 1e-5, (tag, err)
+        assert err <= 1e-4, (tag, err)
     # intensity p u: on the scale max|p| max|u_z| of the fields
     gi = sim.read(focal, I_AVG)
     idx = d["focal_I_idx"].astype(np.int64)
     scale = float(d["field_p_absmax"]) * float(d["field_uz_absmax"])
     err = np.abs(gi[:, idx] - d["focal_I"]).max() / scale
     print("ERRTABLE form=%s config=3 output=focal_I max_err/scale=%.3e" % (form, err))
-    assert err <= 1e-5, err
+    assert err <= 1e-4, err
     for name in ("p", "uz", "rhoz"):
         _sampled(sim.read_field(name).reshape(-1), d, "field_" + name, "field_%s_idx" % name, 1e-3, 5e-3, form)
     sim.close()
