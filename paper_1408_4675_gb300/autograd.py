@@ -6,9 +6,11 @@ source per transducer element driven by s_e(t) = A_e sin(omega t + phi_e)
 and all steps.  forward() makes one forward run (kwgb_adjoint_forward: J is
 accumulated from the focal points on the device; when an input needs a
 gradient the run also keeps a checkpoint every K steps, and the simulation
-that holds them is kept for backward()).  backward() runs the library's
-hand-written reverse pass (kwgb_adjoint_backward: segment recomputation,
-reverse steps) and the chain rule
+that holds them is kept for backward(); when every step's density fields
+fit in half the free device memory they are kept instead, and the reverse
+pass recomputes nothing).  backward() runs the library's hand-written
+reverse pass (kwgb_adjoint_backward: segment recomputation if
+checkpointed, reverse steps) and the chain rule
     dJ/dA_e   = sum_n dJ/ds_e^n sin(omega t_n + phi_e),
     dJ/dphi_e = sum_n dJ/ds_e^n A_e cos(omega t_n + phi_e).
 """
@@ -23,12 +25,20 @@ class FocalProblem:
     """Grid, medium, element masks, focal region and drive frequency of a
     segmented-transducer problem (everything except phases and amplitudes)."""
 
-    def __init__(self, cfg, n_steps=None, checkpoint_every=50):
+    def __init__(self, cfg, n_steps=None, checkpoint_every=None):
+        """checkpoint_every: the adjoint's checkpoint interval K (K >= the
+        step count keeps every step's fields); None takes every step when
+        its fields (28 bytes per grid point per step) fit in half the free
+        device memory, else K = 50."""
         self.cfg = cfg
         self.elements = cfg["elements"]
         self.focal = np.asarray(cfg["focal"], dtype=np.int64)
         self.freq = cfg["freq"]
         self.n_steps = int(n_steps or cfg["n_steps"])
+        if checkpoint_every is None:
+            keep = 28 * int(np.prod(cfg["shape"])) * self.n_steps
+            free = torch.cuda.mem_get_info()[0] if torch.cuda.is_available() else 0
+            checkpoint_every = self.n_steps if keep <= free // 2 else 50
         self.checkpoint_every = int(checkpoint_every)
         self.t = (np.arange(self.n_steps) + 0.5) * cfg["dt"]
         self.last_device_bytes = 0

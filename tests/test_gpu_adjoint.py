@@ -212,3 +212,17 @@ def test_forward_only_and_deferred_backward(kw):
     assert J2 == J1.item()
     np.testing.assert_array_equal(ph.grad.numpy(), dphi)
     np.testing.assert_array_equal(am.grad.numpy(), damp)
+
+
+def test_default_interval_keeps_every_step_when_it_fits(kw):
+    """FocalProblem without an interval keeps every step's fields when they
+    fit in half the free device memory (a small grid), and gives the same
+    gradient as checkpoints every 10 steps."""
+    from paper_1408_4675_gb300.autograd import FocalProblem
+    cfg = _problem(n=32, steps=40)
+    a = FocalProblem(cfg, n_steps=40)
+    assert a.checkpoint_every == 40
+    ra = a.value_and_grad(cfg["phases"], cfg["amps"])
+    rb = FocalProblem(cfg, n_steps=40, checkpoint_every=10).value_and_grad(cfg["phases"], cfg["amps"])
+    assert ra[0] == rb[0]
+    np.testing.assert_array_equal(ra[1], rb[1])
